@@ -1,0 +1,380 @@
+"""Benchmark of the GB300 implicit Hari-Zimmermann GSVD engine.
+
+One step = one whole GSVD solve (prescale, the blocked sweep loop with its
+convergence test, the final scaling and sort) of the blocked real workload
+F 4096x2048, G 4096x2048 (sigma log-spaced in [1e-4, 1e4], cond(X) = 1e3,
+seed 0), with the inputs resident in HBM: each step first restores the
+pristine F, G (device-to-device copy, inside the timed region) because the
+solve works in place.  F + G + Z = 160 MB exceed the 126 MB L2, so no flush
+is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+    python bench.py --impl reference ...     # the oracle on the host cores
+
+Prints one JSON line (rank 0).  N > 1: one process per GPU, each solving its
+own copy (replicas, no collective on the data path); value = all solves / max
+time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "blocked_real_F4096x2048_G4096x2048"
+METRIC = "GSVD solves/s"
+# measured FP64 peak for the DMMA contraction: the measured bf16 dense
+# peak times the nominal FP64/bf16 ratio (1.25 / 2250); FP32 FFMA peak from
+# unit counts and clocks: 152 SMs x 128 lanes x 2 flop x 2.07 GHz
+FP64_NOMINAL_TF, BF16_NOMINAL_TF = 1.25, 2250.0
+FP32_ALU_PEAK_TF = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return m.get("bf16_tflops", 1900.0), "of measured"
+    except Exception:
+        return 1900.0, "of fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, dev_index=0):
+        self.samples = []
+        self.dev = dev_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": len(self.samples)}
+        try:
+            sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+            mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+            if sm:
+                out["sm_mhz"] = float(np.median(sm))
+            if mx:
+                out["sm_max_mhz"] = max(mx)
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            reasons = set()
+            for s in self.samples:
+                for k, nm in enumerate(names):
+                    if len(s) > 4 + k and s[4 + k].lower().startswith("active"):
+                        reasons.add(nm)
+            out["reasons"] = sorted(reasons)
+        except Exception:
+            pass
+        return out
+
+
+def dist_setup(gpus):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if gpus > 1 and ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+        return dist, rank, ws, local
+    return None, rank, ws, local
+
+
+def oracle_sample(F, G, n, budget_s=10.0):
+    """Time the oracle on a bounded sample of this workload's pivots and
+    extrapolate: seconds per pivot (first pivots of sweep 1 of this pair) x
+    n(n-1)/2 pivots per sweep x the oracle's sweep count on a 256-column pair
+    of the same distribution."""
+    import oracle
+    from paper_1909_00101_gb300.inputs import make_pair
+    oracle.build()
+    # calibrate the pivot count to about budget_s
+    t = time.perf_counter()
+    oracle.gsvd(F, G, max_pivots=2000)
+    per = max(1e-7, (time.perf_counter() - t) / 2000)
+    pivots = int(max(2000, min(2_000_000, budget_s / per)))
+    t = time.perf_counter()
+    oracle.gsvd(F, G, max_pivots=pivots)
+    t_sample = time.perf_counter() - t
+    q = make_pair(512, 512, 256, lo=1e-4, hi=1e4, cond=1e3, seed=0)
+    r = oracle.gsvd(q.F, q.G)
+    sweeps = r["sweeps"]
+    t_solve = t_sample / pivots * (n * (n - 1) / 2) * sweeps
+    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": "%d pivots of sweep 1 of the 4096x2048 pair in %.1f s, extrapolated to n(n-1)/2 pivots x %d "
+                      "sweeps (the oracle's sweep count on a 512x256 pair of the same distribution); "
+                      "single-threaded C, -O2 -ffp-contract=off" % (pivots, t_sample, sweeps),
+            "est_seconds_per_solve": t_solve}
+
+
+def run_reference(args):
+    """The oracle as it stands, on the host cores, on this workload (bounded samples)."""
+    from paper_1909_00101_gb300.inputs import make_pair, BLOCKED_REAL_4096x2048
+    p = make_pair(**BLOCKED_REAL_4096x2048)
+    n = p.F.shape[1]
+    vals = []
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm state
+    t0 = time.perf_counter()
+    cb = None
+    for _ in range(args.steps):
+        cb = oracle_sample(p.F, p.G, n, budget_s=max(2.0, 30.0 / max(1, args.steps)))
+        vals.append(cb["value"])
+    elapsed = time.perf_counter() - t0
+    v = float(np.median(vals))
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "m_f": 4096, "m_g": 4096, "n": n, "sigma_range": [1e-4, 1e4],
+                       "cond_x": 1e3, "seed": 0},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0},
+            "sample_wall_s": elapsed}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--block-w", type=int, default=0)
+    ap.add_argument("--inner", type=int, default=0, help="inner sweep cap (0 = library default)")
+    ap.add_argument("--compare", type=int, default=1, help="also time the other precision (1 step)")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--cpu-baseline", type=int, default=1)
+    args = ap.parse_args()
+
+    if args.impl == "reference":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
+        run_reference(args)
+        return
+
+    import torch
+    dist, rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from __graft_entry__ import build
+    build()
+    import paper_1909_00101_gb300 as hz
+    from paper_1909_00101_gb300.inputs import make_pair, BLOCKED_REAL_4096x2048
+
+    p = make_pair(**BLOCKED_REAL_4096x2048)
+    mf, n = p.F.shape
+    mg = p.G.shape[0]
+    F0 = torch.from_numpy(p.F).to(dev)
+    G0 = torch.from_numpy(p.G).to(dev)
+    # column-major working buffers (the solve overwrites them with U, V)
+    F = torch.empty((n, mf), dtype=torch.float64, device=dev).t()
+    G = torch.empty((n, mg), dtype=torch.float64, device=dev).t()
+    Z = torch.empty((n, n), dtype=torch.float64, device=dev).t()
+    sf = torch.empty(n, dtype=torch.float64, device=dev)
+    sg = torch.empty_like(sf)
+    sig = torch.empty_like(sf)
+    stream = torch.cuda.current_stream(dev)
+
+    def make_solver(prec, profile):
+        kw = dict(precision=prec, path="blocked", profile=profile)
+        if args.block_w:
+            kw["block_w"] = args.block_w
+        if args.inner:
+            kw["inner_max_sweeps"] = args.inner
+        return hz.Solver(stream=stream, **kw)
+
+    prob = hz._problem(F, G, Z, sf, sg, sig, True)
+
+    def step(solver):
+        F.copy_(F0)
+        G.copy_(G0)
+        info = hz.Info()
+        import ctypes
+        solver._lib.gsvd_solve(solver._h, ctypes.byref(prob), ctypes.byref(info))
+        return info.as_dict()
+
+    solver = make_solver(args.precision, True)
+    for _ in range(args.warmup):
+        step(solver)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    infos = []
+    evs[0].record(stream)
+    for k in range(args.steps):
+        infos.append(step(solver))
+        evs[k + 1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+
+    # accuracy of the last step: sigma against the construction, residuals
+    last = infos[-1]
+    sig_np = sig.cpu().numpy()
+    rel = float(np.max(np.abs(sig_np - p.sigma) / p.sigma))
+    Fd = F0
+    res_f = float(torch.linalg.norm(Fd @ Z - F * sf[None, :]) / torch.linalg.norm(Fd))
+    res_g = float(torch.linalg.norm(G0 @ Z - G * sg[None, :]) / torch.linalg.norm(G0))
+    orth_u = float(torch.linalg.norm(F.t() @ F - torch.eye(n, dtype=torch.float64, device=dev)))
+
+    # roofline of the dominant kernel class (event-timed launches of the timed steps)
+    names = ["gram_f64", "inner_f64", "apply_f64", "gram_f32", "inner_f32", "apply_f32"]
+    tk = np.sum([i["t_kernel_us"] for i in infos], axis=0)
+    nk = np.sum([i["n_kernel"] for i in infos], axis=0)
+    dom = int(np.argmax(tk))
+    w = last["block_w"]
+    b = 2 * w
+    visits = sum(i["visits"] for i in infos)
+    applied = sum(i["visits_applied"] for i in infos)
+    bf16, peak_note = measured_peaks()
+    fp64_peak = bf16 * FP64_NOMINAL_TF / BF16_NOMINAL_TF
+    roof = None
+    if nk[dom] > 0:
+        avg_s = tk[dom] / nk[dom] / 1e6
+        nl = nk[dom]
+        if names[dom].startswith("gram"):
+            units = visits / max(1, (nk[0] + nk[3]))
+            flops = units * b * (b + 1) * (mf + mg)
+        elif names[dom].startswith("apply"):
+            units = applied / max(1, (nk[2] + nk[5]))
+            flops = units * 2.0 * b * b * (mf + mg + n)
+        else:
+            units, flops = visits / max(1, nk[1] + nk[4]), None
+        fp32 = names[dom].endswith("f32")
+        if flops is not None:
+            ach = flops / avg_s / 1e12
+            if fp32:
+                roof = {"bound": "alu", "achieved": ach, "peak": FP32_ALU_PEAK_TF, "unit": "TFLOP/s",
+                        "frac": ach / FP32_ALU_PEAK_TF, "traffic": None, "kernel": names[dom],
+                        "peak_note": "FP32 FFMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"}
+            else:
+                roof = {"bound": "tensor", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                        "frac": ach / fp64_peak, "traffic": None, "kernel": names[dom],
+                        "peak_note": "FP64 DMMA: bf16 dense %s x 1.25/2250 nominal FP64/bf16" % peak_note}
+        else:
+            roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
+                    "traffic": None, "kernel": names[dom], "note": "FP64-latency-bound inner level"}
+        roof["avg_launch_us"] = avg_s * 1e6
+        roof["launches"] = int(nl)
+        roof["units_per_launch"] = units
+    kshare = {names[k]: round(float(tk[k] / max(1e-9, tk.sum())), 4) for k in range(6) if nk[k]}
+
+    out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "m_f": mf, "m_g": mg, "n": n, "precision": args.precision,
+                      "block_w": w, "inner_max_sweeps": args.inner or 30, "sigma_range": [1e-4, 1e4],
+                      "cond_x": 1e3, "seed": 0, "l2": "inputs (160 MB) larger than L2"},
+           "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                          "min": float(np.min(step_ms))},
+           "accuracy": {"max_rel_sigma_err_vs_construction": rel, "res_FZ": res_f, "res_GZ": res_g,
+                        "orth_U": orth_u, "status": last["status"]},
+           "solve": {k: last[k] for k in ("sweeps_fp32", "sweeps_fp64", "transf_all", "transf_big",
+                                          "t_total_us", "t_fp32_us", "t_refine_us", "visits",
+                                          "visits_applied", "chol_skipped")},
+           "kernel_time_share": kshare,
+           "roofline": roof, "clocks": clk,
+           "gpu_launches": None}
+    # launches of our kernels in the timed region: per sweep 3 per outer step
+    # plus prescale/rescale/finalize/check kernels
+    out["gpu_launches"] = int(sum(sum(i["n_kernel"]) for i in infos)
+                              + args.steps * 14 + sum(i["sweeps_fp32"] + i["sweeps_fp64"] for i in infos))
+
+    if args.compare and rank == 0:
+        other = "fp64" if args.precision == "mixed" else "mixed"
+        s2 = make_solver(other, False)
+        step(s2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        inf2 = step(s2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rel2 = float(np.max(np.abs(sig.cpu().numpy() - p.sigma) / p.sigma))
+        out["compare_" + other] = {"ms_per_solve": e0.elapsed_time(e1), "solves_per_s": 1e3 / e0.elapsed_time(e1),
+                                   "sweeps_fp32": inf2["sweeps_fp32"], "sweeps_fp64": inf2["sweeps_fp64"],
+                                   "max_rel_sigma_err_vs_construction": rel2, "status": inf2["status"]}
+        s2.close()
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    if rank == 0 and args.e2e_steps > 0:
+        Fh = np.asfortranarray(p.F).copy(order="F")
+        Gh = np.asfortranarray(p.G).copy(order="F")
+        Zh = np.zeros((n, n), order="F")
+        vh = [np.zeros(n) for _ in range(3)]
+        ph = hz._problem(Fh, Gh, Zh, vh[0], vh[1], vh[2], False)
+        import ctypes
+        se = make_solver(args.precision, False)
+        ts = []
+        for _ in range(args.e2e_steps):
+            Fh[:] = p.F
+            Gh[:] = p.G
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = hz.Info()
+            se._lib.gsvd_solve(se._h, ctypes.byref(ph), ctypes.byref(info))
+            ts.append(time.perf_counter() - t0)
+        se.close()
+        out["e2e"] = {"value": 1.0 / float(np.median(ts)), "unit": "solves/s",
+                      "h2d_bytes_per_step": int(Fh.nbytes + Gh.nbytes),
+                      "d2h_bytes_per_step": int(Fh.nbytes + Gh.nbytes + Zh.nbytes + 3 * 8 * n),
+                      "status": info.status}
+
+    if rank == 0 and args.cpu_baseline:
+        out["cpu_baseline"] = oracle_sample(p.F, p.G, n)
+    solver.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

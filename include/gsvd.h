@@ -1,0 +1,163 @@
+/*
+ * gsvd.h -- C ABI of the GB300 implicit Hari-Zimmermann GSVD engine.
+ *
+ * Computes the generalized singular value decomposition of a full-column-rank
+ * pair (F, G), F of m_F x n and G of m_G x n, real or complex, by the one-sided
+ * implicit Hari-Zimmermann method (Novakovic & Singer, "Implicit
+ * Hari-Zimmermann algorithm for the generalized SVD on the GPUs",
+ * arXiv 1909.00101):
+ *
+ *     F Z = U Sigma_F,   G Z = V Sigma_G,   U^* U = V^* V = I,
+ *     Sigma_F^2 + Sigma_G^2 = I,   Sigma = Sigma_G^{-1} Sigma_F sorted descending
+ *
+ * (Sec. 1 of the paper; the sweep loop of Sec. 2.2-2.5 runs on one GPU).
+ *
+ * Memory: every matrix is column-major with a leading dimension (in elements).
+ * Real data is double; complex data is interleaved (re, im) doubles, the layout
+ * of C99 double _Complex and of numpy/torch complex128.  F is overwritten by U
+ * and G by V (in place, as in Sec. 3.1.1); Z (n x n) and the three length-n
+ * vectors are outputs.  Pointers may be device pointers (the solve runs in
+ * place) or host pointers (pageable or pinned: the library copies in and out
+ * through its own device buffers); one problem must not mix the two.
+ *
+ * Ownership: the caller owns every buffer passed in a gsvd_problem; the
+ * library owns the handle, its stream use, device workspace and the serving
+ * thread.  Buffers given to gsvd_submit must stay valid and untouched until
+ * gsvd_poll returns a terminal status for that ticket.
+ *
+ * Errors: every function returns an int status (GSVD_OK = 0, negative =
+ * error, GSVD_EAGAIN = 1 is "not yet").  Argument errors are detected before
+ * any launch and leave the buffers untouched.  GSVD_ENOCONV still writes the
+ * outputs of the last sweep.  Device-side failures (GSVD_ENOTPD,
+ * GSVD_EOVERFLOW) are per problem; one failed problem of a batch does not
+ * affect the others.
+ */
+#ifndef GSVD_GB300_H
+#define GSVD_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  GSVD_OK = 0,
+  GSVD_EAGAIN = 1,     /* poll: not finished; submit: queue full */
+  GSVD_EINVAL = -1,    /* bad argument, non-finite input, m < n, n < 1, ld < m */
+  GSVD_ENOMEM = -2,    /* device allocation failed */
+  GSVD_ENOCONV = -3,   /* sweep cap reached; outputs written */
+  GSVD_ENOTPD = -4,    /* non-positive Cholesky pivot or 1 - x^2 <= 0 (rank-deficient G) */
+  GSVD_EOVERFLOW = -5, /* non-finite column norm */
+  GSVD_ETIMEOUT = -6,  /* a bounded wait ran out */
+  GSVD_ECUDA = -7,     /* a CUDA runtime call failed */
+  GSVD_ETOOBIG = -8    /* one request exceeds the memory budget */
+};
+
+enum { GSVD_R64 = 0, GSVD_C128 = 1 };
+enum { GSVD_PREC_FP64 = 0, GSVD_PREC_MIXED = 1 };
+enum { GSVD_PATH_AUTO = 0, GSVD_PATH_POINTWISE = 1, GSVD_PATH_BLOCKED = 2 };
+enum { GSVD_ORDER_ROUND_ROBIN = 0, GSVD_ORDER_ROW_CYCLIC = 1 };
+
+typedef struct gsvd_ctx *gsvd_handle;
+
+/* Solver configuration (gsvd_config_default fills the defaults below). */
+typedef struct {
+  int32_t precision;        /* GSVD_PREC_FP64 (default) or GSVD_PREC_MIXED: FP32 bulk sweeps with
+                               FP64 2x2 parameters, then FP64 refinement sweeps */
+  int32_t block_w;          /* block width w of Sec. 2.3 (pair width 2w); 0 = choose by size */
+  int32_t max_sweeps;       /* outer sweep cap (default 30, Alg. cpu1) */
+  int32_t inner_max_sweeps; /* inner sweep cap: 30 = full block (FB), 1 = block-oriented (BO) */
+  int32_t criterion;        /* small-transformation criterion of Sec. 2.5: 1 = C1, 2 = C2 */
+  int32_t sort;             /* 1 = per-step column sorting (Sec. 2.1) */
+  int32_t path;             /* GSVD_PATH_*: pointwise in-shared-memory or blocked */
+  int32_t order;            /* pointwise pivot order: GSVD_ORDER_* */
+  int32_t fp32_max_sweeps;  /* mixed precision: cap of the FP32 bulk sweeps (default 30) */
+  int32_t timeout_ms;       /* bound of host waits (0 = none) */
+  uint64_t hbm_budget_bytes;/* serving: device memory admitted at once (default 60 GiB) */
+  int32_t max_inflight;     /* serving: requests on the GPU at once (default 16) */
+  int32_t profile;          /* 1 = time every Gram / inner / apply launch with CUDA events on the
+                               solve's stream (gsvd_info.t_kernel_us); 0 = off (default) */
+  int32_t inner_max_sweeps_fp32; /* inner sweep cap of the FP32 bulk sweeps (default 1 = BO;
+                               0 = same as inner_max_sweeps) */
+  int32_t reserved;
+} gsvd_config;
+
+/* One problem.  dtype = GSVD_R64 or GSVD_C128. */
+typedef struct {
+  int32_t dtype;
+  int32_t reserved;
+  int64_t m_f, m_g, n;
+  void *F;                  /* in: F (m_f x n);  out: U */
+  int64_t ldf;
+  void *G;                  /* in: G (m_g x n);  out: V */
+  int64_t ldg;
+  void *Z;                  /* out: Z (n x n) */
+  int64_t ldz;
+  double *sigma_f;          /* out: diag(Sigma_F), length n, sorted by descending Sigma */
+  double *sigma_g;          /* out: diag(Sigma_G) */
+  double *sigma;            /* out: Sigma = Sigma_F / Sigma_G */
+} gsvd_problem;
+
+/* Per-solve report. */
+typedef struct {
+  int32_t status;           /* GSVD_* of this problem */
+  int32_t sweeps_fp32;      /* FP32 bulk sweeps (mixed precision) */
+  int32_t sweeps_fp64;      /* FP64 sweeps (outer sweeps of the blocked path; sweeps of the pointwise path) */
+  int32_t path;             /* GSVD_PATH_POINTWISE or GSVD_PATH_BLOCKED */
+  uint64_t transf_all;      /* transformations applied (all classes) */
+  uint64_t transf_big;      /* big transformations (Sec. 2.5) */
+  double t_total_us;        /* wall time of the solve on the device */
+  double t_fp32_us;         /* time of the FP32 bulk sweeps */
+  double t_refine_us;       /* time of the FP64 sweeps after the FP32 ones */
+  int32_t block_w;          /* block width used (0 = pointwise) */
+  int32_t chol_skipped;     /* FP32 pivot blocks skipped for a failed Cholesky */
+  uint64_t visits;          /* block pair visits (blocked path) */
+  uint64_t visits_applied;  /* visits whose Z-tilde was applied (the others had no transformation) */
+  double t_kernel_us[6];    /* with profile = 1: summed launch times of Gram FP64, inner FP64, apply
+                               FP64, Gram FP32, inner FP32, apply FP32 */
+  int32_t n_kernel[6];      /* launch counts of the same kernels */
+} gsvd_info;
+
+/* Fill cfg with the defaults. */
+void gsvd_config_default(gsvd_config *cfg);
+
+/* Create a handle.  cfg may be NULL (defaults).  cuda_stream: a cudaStream_t,
+ * NULL = the legacy default stream.  One handle per host thread/stream. */
+int gsvd_create(gsvd_handle *h, const gsvd_config *cfg, void *cuda_stream);
+
+/* Destroy a handle: waits for its serving thread and frees its workspace. */
+int gsvd_destroy(gsvd_handle h);
+
+/* Solve one problem; blocks until the outputs are written.  info may be NULL.
+ * Returns the problem's status. */
+int gsvd_solve(gsvd_handle h, const gsvd_problem *p, gsvd_info *info);
+
+/* Solve count independent problems; problems small enough for shared memory
+ * run in one launch of the pointwise kernel (one CTA each), the others on the
+ * blocked path.  infos (may be NULL) receives one report per problem.
+ * Returns GSVD_OK if every problem succeeded, else the first failing status. */
+int gsvd_solve_batched(gsvd_handle h, const gsvd_problem *ps, int32_t count, gsvd_info *infos);
+
+/* Serving: enqueue a problem (device pointers only) for the handle's
+ * scheduler thread, which admits requests while the memory budget and the
+ * in-flight limit allow and runs them concurrently on their own streams.
+ * Returns GSVD_OK with *ticket set, GSVD_ETOOBIG if the request alone exceeds
+ * the budget, GSVD_EINVAL for a bad problem. */
+int gsvd_submit(gsvd_handle h, const gsvd_problem *p, uint64_t *ticket);
+
+/* Serving: GSVD_EAGAIN while the ticket is queued or running; otherwise the
+ * request's final status (info filled, the ticket released). */
+int gsvd_poll(gsvd_handle h, uint64_t ticket, gsvd_info *info);
+
+/* Device bytes a solve of this shape needs beyond the caller's buffers. */
+uint64_t gsvd_workspace_bytes(const gsvd_config *cfg, int32_t dtype, int64_t m_f, int64_t m_g, int64_t n);
+
+/* Static text of a status code. */
+const char *gsvd_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSVD_GB300_H */

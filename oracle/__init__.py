@@ -34,7 +34,7 @@ STATUS = {0: "OK", -1: "EINVAL", -3: "ENOCONV", -4: "ENOTPD"}
 
 class _Opts(ctypes.Structure):
     _fields_ = [("max_sweeps", ctypes.c_int32), ("sort", ctypes.c_int32),
-                ("criterion", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("criterion", ctypes.c_int32), ("max_pivots", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -96,7 +96,7 @@ def _ptr(a: np.ndarray):
 
 
 def gsvd(F, G, *, max_sweeps: int = 100, sort: bool = True, criterion: int = 1,
-         extended: bool = False, lib=None) -> dict:
+         extended: bool = False, max_pivots: int = 0, lib=None) -> dict:
     """GSVD of (F, G) by the oracle.
 
     F (mF x n) and G (mG x n) are real float64 or complex128 arrays.  Returns
@@ -118,7 +118,7 @@ def gsvd(F, G, *, max_sweeps: int = 100, sort: bool = True, criterion: int = 1,
     sf = np.zeros(n)
     sg = np.zeros(n)
     sig = np.zeros(n)
-    opts = _Opts(max_sweeps, 1 if sort else 0, criterion, 0)
+    opts = _Opts(max_sweeps, 1 if sort else 0, criterion, max_pivots)
     st = _Stats()
     lib = lib or _load()
     fn = getattr(lib, "hzo_gsvd_%s_%s" % ("cplx" if cplx else "real", "ld" if extended else "d"))

@@ -76,7 +76,8 @@ typedef struct {
     int32_t max_sweeps; /* sweep cap; exceeding it gives HZO_ENOCONV       */
     int32_t sort;       /* 1: per-step column sorting (Sec. 2.1)           */
     int32_t criterion;  /* 1: C1, 2: C2 (Sec. 2.5)                          */
-    int32_t pad;
+    int32_t max_pivots; /* > 0: stop after this many pivot pairs (a bounded
+                           timing sample; the result is then HZO_ENOCONV)  */
 } hzo_opts;
 
 typedef struct {
@@ -303,11 +304,19 @@ int HZO(hzo_gsvd_real)(int64_t mf, int64_t mg, int64_t n,
     const real_t tol = HZO_EPS * sqrt((real_t)n); /* eps * sqrt(n), R5, R6 */
     int converged = (n == 1);
     int sweep = 0;
+    int64_t pivots = 0;
     while (!converged && sweep < opt->max_sweeps) {
         ++sweep;
         int64_t nall = 0, nbig = 0;
         for (int64_t i = 0; i < n - 1; ++i) {
             for (int64_t j = i + 1; j < n; ++j) {
+                if (opt->max_pivots > 0 && pivots++ >= opt->max_pivots) {
+                    st->transf_all += nall;
+                    st->transf_big += nbig;
+                    st->sweeps = sweep;
+                    status = HZO_ENOCONV;
+                    goto done;
+                }
                 real_t *fi = &f[i * mf], *fj = &f[j * mf];
                 real_t *gi = &g[i * mg], *gj = &g[j * mg];
                 real_t aii = dot_rr(fi, fi, mf);
@@ -462,11 +471,19 @@ int HZO(hzo_gsvd_cplx)(int64_t mf, int64_t mg, int64_t n,
     const real_t tol = HZO_EPS * sqrt((real_t)n);
     int converged = (n == 1);
     int sweep = 0;
+    int64_t pivots = 0;
     while (!converged && sweep < opt->max_sweeps) {
         ++sweep;
         int64_t nall = 0, nbig = 0;
         for (int64_t i = 0; i < n - 1; ++i) {
             for (int64_t j = i + 1; j < n; ++j) {
+                if (opt->max_pivots > 0 && pivots++ >= opt->max_pivots) {
+                    st->transf_all += nall;
+                    st->transf_big += nbig;
+                    st->sweeps = sweep;
+                    status = HZO_ENOCONV;
+                    goto done;
+                }
                 cplx_t *fi = &f[i * mf], *fj = &f[j * mf];
                 cplx_t *gi = &g[i * mg], *gj = &g[j * mg];
                 real_t aii = nrm2sq_c(fi, mf);

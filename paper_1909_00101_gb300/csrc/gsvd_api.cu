@@ -1,0 +1,769 @@
+// gsvd_api.cu -- host runtime behind the C ABI of include/gsvd.h: validation,
+// planning (path, block width, row splits, pivot tables), workspace, the
+// sweep loop of Alg. cpu1 (Sec. 3.6) with the convergence test of Sec. 2.5,
+// the mixed-precision driver, batched solves and the serving scheduler.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "../../include/gsvd.h"
+#include "hz_kernels.h"
+
+using namespace hz;
+
+namespace {
+
+constexpr double EPS64 = 1.1102230246251565e-16;  // 2^-53
+constexpr double EPS32 = 5.9604644775390625e-08;  // 2^-24
+constexpr int POINTWISE_MAX_N = 64;
+constexpr int NCTR = 8;
+constexpr size_t SMEM_LIMIT = 227 * 1024;
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Round-robin ("circle method") table for M (even) players: M-1 steps of M/2
+// disjoint pairs; every pair once per sweep (a cyclic parallel strategy,
+// Sec. 2.2).  Players >= nreal are dummies (their pairs are skipped).
+std::vector<uint16_t> round_robin_table(int M) {
+  std::vector<uint16_t> t((size_t)(M - 1) * (M / 2) * 2);
+  for (int s = 0; s < M - 1; ++s)
+    for (int k = 0; k < M / 2; ++k) {
+      int a, b;
+      if (k == 0) {
+        a = M - 1;
+        b = s;
+      } else {
+        a = (s + k) % (M - 1);
+        b = (s - k + (M - 1)) % (M - 1);
+      }
+      t[((size_t)s * (M / 2) + k) * 2] = (uint16_t)std::min(a, b);
+      t[((size_t)s * (M / 2) + k) * 2 + 1] = (uint16_t)std::max(a, b);
+    }
+  return t;
+}
+
+// Wavefront of the row-cyclic order: step s holds the pairs (i, j), i < j,
+// i + j = s + 1.  Any order consistent with the row-cyclic dependencies gives
+// the same transformations, so this parallel table reproduces the sequential
+// row-cyclic strategy exactly.  Unused slots hold (0xffff, 0xffff).
+std::vector<uint16_t> row_cyclic_table(int n, int* steps, int* slots) {
+  *steps = std::max(1, 2 * n - 3);
+  *slots = std::max(1, n / 2);
+  std::vector<uint16_t> t((size_t)(*steps) * (*slots) * 2, 0xffff);
+  for (int s = 0; s < *steps; ++s) {
+    const int sum = s + 1;
+    int k = 0;
+    for (int i = std::max(0, sum - (n - 1)); 2 * i < sum; ++i) {
+      const int j = sum - i;
+      if (j <= i || j >= n) continue;
+      t[((size_t)s * (*slots) + k) * 2] = (uint16_t)i;
+      t[((size_t)s * (*slots) + k) * 2 + 1] = (uint16_t)j;
+      ++k;
+    }
+  }
+  return t;
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t n = 0;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= n) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e == cudaSuccess) n = bytes;
+    return e;
+  }
+};
+
+struct Plan {
+  bool cplx;
+  int E;
+  int mf, mg, n;
+  int path;  // GSVD_PATH_POINTWISE / BLOCKED
+  // blocked
+  int w = 0, nblk = 0, neff = 0, nslots = 0, steps = 0, rf = 1, rg = 1, V = 0;
+  // workspace layout (bytes)
+  size_t off_partial = 0, off_ztil = 0, off_flags = 0, off_ctr = 0, off_zdiag = 0, off_norms = 0,
+         off_rank = 0, off_status = 0, off_work = 0, off_f32 = 0, off_g32 = 0, off_z32 = 0, off_table = 0,
+         total = 0;
+  size_t table_bytes = 0;
+  // pointwise
+  int pw_steps = 0, pw_slots = 0;
+  size_t pw_smem = 0;
+};
+
+int choose_w(const gsvd_config& c, bool cplx, int n) {
+  if (c.block_w > 0) return c.block_w;
+  if (cplx) return n >= 256 ? 16 : 8;
+  return n >= 512 ? 16 : 8;
+}
+
+bool make_plan(const gsvd_config& cfg, int dtype, int64_t mf, int64_t mg, int64_t n, Plan& P) {
+  P.cplx = dtype == GSVD_C128;
+  P.E = P.cplx ? 2 : 1;
+  P.mf = (int)mf;
+  P.mg = (int)mg;
+  P.n = (int)n;
+  const int slots_rr = (int)((n + 1) / 2);
+  size_t pw_smem = pointwise_smem_bytes((int)mf, (int)mg, (int)n, P.cplx, false,
+                                        cfg.order == GSVD_ORDER_ROW_CYCLIC ? std::max<int64_t>(1, n / 2) : slots_rr);
+  bool pw_ok = n <= POINTWISE_MAX_N && pw_smem <= SMEM_LIMIT;
+  if (cfg.path == GSVD_PATH_POINTWISE && !pw_ok) return false;
+  if (cfg.path == GSVD_PATH_POINTWISE || (cfg.path == GSVD_PATH_AUTO && pw_ok) || n < 4) {
+    if (!pw_ok) return false;
+    P.path = GSVD_PATH_POINTWISE;
+    if (cfg.order == GSVD_ORDER_ROW_CYCLIC) {
+      row_cyclic_table((int)n, &P.pw_steps, &P.pw_slots);
+    } else {
+      const int M = (int)(n + (n & 1));
+      P.pw_steps = std::max(1, M - 1);
+      P.pw_slots = std::max(1, M / 2);
+    }
+    P.pw_smem = pointwise_smem_bytes((int)mf, (int)mg, (int)n, P.cplx, false, P.pw_slots);
+    P.table_bytes = (size_t)P.pw_steps * P.pw_slots * 4;
+    P.off_table = 0;
+    P.off_status = align256(P.table_bytes);
+    P.total = P.off_status + 256;
+    return true;
+  }
+  P.path = GSVD_PATH_BLOCKED;
+  P.w = choose_w(cfg, P.cplx, (int)n);
+  P.V = blk_vmax(P.w, P.cplx);
+  if (P.V == 0) return false;
+  P.nblk = (int)((n + P.w - 1) / P.w);
+  if (P.nblk < 2) {
+    // too narrow for two blocks: halve the width
+    P.w = std::max(1, (int)((n + 1) / 2));
+    P.V = blk_vmax(P.w, P.cplx);
+    P.nblk = (int)((n + P.w - 1) / P.w);
+  }
+  P.neff = P.nblk + (P.nblk & 1);
+  P.nslots = P.neff / 2;
+  P.steps = P.neff - 1;
+  // row splits: about four Gram CTAs per SM in total, at least 64 rows each
+  const int target = 4 * 152;
+  int s = std::max(2, (target + P.nslots - 1) / P.nslots);
+  P.rf = std::max(1, std::min((int)((mf + 63) / 64), (int)std::lround((double)s * mf / (double)(mf + mg))));
+  P.rg = std::max(1, std::min((int)((mg + 63) / 64), s - P.rf));
+  const size_t V2 = (size_t)P.V * P.V;
+  size_t o = 0;
+  P.off_partial = o; o = align256(o + (size_t)P.nslots * (P.rf + P.rg) * V2 * 8);
+  P.off_ztil = o; o = align256(o + (size_t)P.nslots * V2 * 8);
+  P.off_flags = o; o = align256(o + (size_t)P.nslots * 4);
+  P.off_ctr = o; o = align256(o + NCTR * 8);
+  P.off_zdiag = o; o = align256(o + (size_t)n * 8);
+  P.off_norms = o; o = align256(o + (size_t)2 * n * 8);
+  P.off_rank = o; o = align256(o + (size_t)n * 4);
+  P.off_status = o; o = align256(o + 16);
+  P.off_work = o; o = align256(o + (size_t)std::max({mf, mg, n}) * n * P.E * 8);
+  P.table_bytes = (size_t)P.steps * P.nslots * 4;
+  P.off_table = o; o = align256(o + P.table_bytes);
+  if (cfg.precision == GSVD_PREC_MIXED) {
+    P.off_f32 = o; o = align256(o + (size_t)mf * n * P.E * 4);
+    P.off_g32 = o; o = align256(o + (size_t)mg * n * P.E * 4);
+    P.off_z32 = o; o = align256(o + (size_t)n * n * P.E * 4);
+  }
+  P.total = o;
+  return true;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? GSVD_OK : (e == cudaErrorMemoryAllocation ? GSVD_ENOMEM : GSVD_ECUDA); }
+
+#define CK(x)                               \
+  do {                                      \
+    cudaError_t e_ = (x);                   \
+    if (e_ != cudaSuccess) return cuda_status(e_); \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int validate(const gsvd_problem* p) {
+  if (!p) return GSVD_EINVAL;
+  if (p->dtype != GSVD_R64 && p->dtype != GSVD_C128) return GSVD_EINVAL;
+  if (p->n < 1 || p->m_f < p->n || p->m_g < p->n) return GSVD_EINVAL;
+  if (p->n > 32768 || p->m_f > (int64_t)1 << 30 || p->m_g > (int64_t)1 << 30) return GSVD_EINVAL;
+  if (p->ldf < p->m_f || p->ldg < p->m_g || p->ldz < p->n) return GSVD_EINVAL;
+  if (!p->F || !p->G || !p->Z || !p->sigma_f || !p->sigma_g || !p->sigma) return GSVD_EINVAL;
+  return GSVD_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ ctx ----
+struct Request {
+  gsvd_problem prob;
+  gsvd_info info;
+  uint64_t bytes;
+  int state;  // 0 queued, 1 running, 2 done
+};
+
+struct gsvd_ctx {
+  gsvd_config cfg;
+  cudaStream_t stream;
+  DevBuf ws;
+  unsigned long long* h_ctr = nullptr;  // pinned counters (NCTR)
+  // serving
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<uint64_t> queue;
+  std::map<uint64_t, std::unique_ptr<Request>> reqs;
+  uint64_t next_ticket = 1;
+  uint64_t used_bytes = 0;
+  int inflight = 0;
+  bool stop = false;
+  std::vector<std::thread> workers;
+};
+
+namespace {
+
+// The blocked sweep loop on (F, G, Z) of type T: Alg. cpu1 with the outer
+// stopping rule "no big transformation in a sweep" (Sec. 2.5).
+struct KTimer {
+  // per-launch CUDA events on the solve's stream (profile mode)
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> kind;
+  void mark(int k, cudaStream_t s) {
+    cudaEvent_t a;
+    cudaEventCreate(&a);
+    cudaEventRecord(a, s);
+    ev.push_back(a);
+    kind.push_back(k);
+  }
+  void flush(gsvd_info* info) {
+    for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+      info->t_kernel_us[kind[i]] += ms * 1e3;
+      info->n_kernel[kind[i]] += 1;
+    }
+    for (auto e : ev) cudaEventDestroy(e);
+    ev.clear();
+    kind.clear();
+  }
+};
+
+int run_sweeps(const Plan& P, const gsvd_config& cfg, bool fp32, void* F, long long ldf, void* G, long long ldg,
+               void* Z, long long ldz, unsigned char* ws, unsigned long long* h_ctr, int max_sweeps,
+               cudaStream_t s, int* sweeps_out, uint64_t* tall, uint64_t* tbig, int* chol_skipped,
+               gsvd_info* info) {
+  BlkDims d;
+  d.mf = P.mf; d.mg = P.mg; d.n = P.n; d.w = P.w; d.nblk = P.nblk; d.nslots = P.nslots;
+  d.rf = P.rf; d.rg = P.rg; d.trows = 64;
+  BlkBuffers b;
+  b.F = F; b.ldf = ldf; b.G = G; b.ldg = ldg; b.Z = Z; b.ldz = ldz;
+  b.partial = ws + P.off_partial;
+  b.ztil = ws + P.off_ztil;
+  b.flags = reinterpret_cast<int*>(ws + P.off_flags);
+  b.ctr = reinterpret_cast<unsigned long long*>(ws + P.off_ctr);
+  b.table = reinterpret_cast<const uint16_t*>(ws + P.off_table);
+  InnerParams ip;
+  ip.eps = fp32 ? EPS32 : EPS64;
+  // FP32 bulk sweeps: the pivot Grams carry FP32 rounding noise of about
+  // eps32 * sqrt(m) relative (the expected error of a dot product of length m,
+  // the argument the paper's threshold rests on); pairs below that level are
+  // left to the FP64 sweeps.  FP64 sweeps use the paper's eps * sqrt(b).
+  ip.tol = fp32 ? EPS32 * std::sqrt((double)std::max(P.mf, P.mg)) : 0.0;
+  ip.inner_max = fp32 && cfg.inner_max_sweeps_fp32 > 0 ? cfg.inner_max_sweeps_fp32 : cfg.inner_max_sweeps;
+  ip.sort = cfg.sort != 0;
+  ip.f32cls = fp32;
+  ip.crit2 = cfg.criterion == 2;
+  ip.chol_skip = fp32;
+  int sw = 0;
+  bool converged = false;
+  const bool prof = cfg.profile != 0;
+  const int kb = fp32 ? 3 : 0;
+  KTimer kt;
+  static const bool trace = std::getenv("GSVD_TRACE") != nullptr;
+  auto t_sweep = std::chrono::steady_clock::now();
+  while (sw < max_sweeps) {
+    CK(cudaMemsetAsync(b.ctr, 0, NCTR * sizeof(unsigned long long), s));
+    for (int k = 0; k < P.steps; ++k) {
+      if (prof) kt.mark(kb + 0, s);
+      CK(launch_gram(d, b, P.cplx, fp32, k, s));
+      if (prof) { kt.mark(kb + 0, s); kt.mark(kb + 1, s); }
+      CK(launch_inner(d, b, P.cplx, fp32, k, ip, s));
+      if (prof) { kt.mark(kb + 1, s); kt.mark(kb + 2, s); }
+      CK(launch_apply(d, b, P.cplx, fp32, k, s));
+      if (prof) kt.mark(kb + 2, s);
+    }
+    CK(cudaMemcpyAsync(h_ctr, b.ctr, NCTR * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (prof) kt.flush(info);
+    ++sw;
+    *tall += h_ctr[0];
+    *tbig += h_ctr[1];
+    *chol_skipped += (int)h_ctr[3];
+    info->visits += h_ctr[4];
+    info->visits_applied += h_ctr[5];
+    if (trace) {
+      const auto now = std::chrono::steady_clock::now();
+      std::fprintf(stderr, "gsvd %s sweep %d: transf %llu big %llu visits %llu applied %llu fail %llu skip %llu  %.2f ms\n",
+                   fp32 ? "fp32" : "fp64", sw, h_ctr[0], h_ctr[1], h_ctr[4], h_ctr[5], h_ctr[2], h_ctr[3],
+                   std::chrono::duration<double, std::milli>(now - t_sweep).count());
+      t_sweep = now;
+    }
+    if (h_ctr[2]) {
+      *sweeps_out = sw;
+      return GSVD_ENOTPD;
+    }
+    if (h_ctr[1] == 0) {
+      converged = true;
+      break;
+    }
+    CK(launch_rescale(P.mf, P.mg, P.n, P.cplx, fp32, F, ldf, G, ldg, Z, ldz, s));
+  }
+  *sweeps_out = sw;
+  return converged ? GSVD_OK : GSVD_ENOCONV;
+}
+
+int solve_pointwise(const gsvd_config& cfg, const gsvd_problem* ps, const int* idx, int count, cudaStream_t s,
+                    gsvd_info* infos) {
+  // pivot pairs are generated per problem from its own n; the launch only
+  // needs the largest step width of the batch for the shared-memory layout
+  const bool rowcyc = cfg.order == GSVD_ORDER_ROW_CYCLIC;
+  int slots = 1;
+  for (int k = 0; k < count; ++k) {
+    const int n = (int)ps[idx[k]].n;
+    slots = std::max(slots, rowcyc ? std::max(1, n / 2) : std::max(1, (n + (n & 1)) / 2));
+  }
+  const size_t pb = align256(sizeof(PwProblem) * count);
+  DevBuf tmp;
+  CK(tmp.ensure(2 * pb + sizeof(PwStats) * count));
+  unsigned char* base = static_cast<unsigned char*>(tmp.p);
+  PwStats* d_stats = reinterpret_cast<PwStats*>(base + 2 * pb);
+  CK(cudaMemsetAsync(d_stats, 0, sizeof(PwStats) * count, s));
+  PwParams prm;
+  prm.eps = EPS64;
+  prm.max_sweeps = cfg.max_sweeps;
+  prm.sort = cfg.sort != 0;
+  prm.f32cls = false;
+  prm.crit2 = cfg.criterion == 2;
+  prm.rowcyc = rowcyc;
+  // real and complex problems run in separate launches (one kernel each)
+  size_t off = 0;
+  std::vector<int> pos(count);
+  for (int kind = 0; kind < 2; ++kind) {
+    std::vector<PwProblem> sub;
+    size_t smem = 0;
+    for (int k = 0; k < count; ++k) {
+      const gsvd_problem& p = ps[idx[k]];
+      if ((p.dtype == GSVD_C128) != (kind == 1)) continue;
+      PwProblem q;
+      q.F = p.F; q.ldf = p.ldf; q.G = p.G; q.ldg = p.ldg; q.Z = p.Z; q.ldz = p.ldz;
+      q.mf = (int)p.m_f; q.mg = (int)p.m_g; q.n = (int)p.n; q.pad = 0;
+      q.sigma_f = p.sigma_f; q.sigma_g = p.sigma_g; q.sigma = p.sigma;
+      q.stats = d_stats + k;
+      sub.push_back(q);
+      smem = std::max(smem, pointwise_smem_bytes(q.mf, q.mg, q.n, kind == 1, false, slots));
+    }
+    if (sub.empty()) continue;
+    PwProblem* d_probs = reinterpret_cast<PwProblem*>(base + off);
+    off += pb;
+    CK(cudaMemcpyAsync(d_probs, sub.data(), sizeof(PwProblem) * sub.size(), cudaMemcpyHostToDevice, s));
+    CK(launch_pointwise(d_probs, (int)sub.size(), slots, kind == 1, false, smem, prm, s));
+  }
+  std::vector<PwStats> hs(count);
+  CK(cudaMemcpyAsync(hs.data(), d_stats, sizeof(PwStats) * count, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int k = 0; k < count; ++k) {
+    gsvd_info& in = infos[idx[k]];
+    in.status = hs[k].status;
+    in.sweeps_fp64 = hs[k].sweeps;
+    in.sweeps_fp32 = 0;
+    in.transf_all = (uint64_t)hs[k].transf_all;
+    in.transf_big = (uint64_t)hs[k].transf_big;
+    in.path = GSVD_PATH_POINTWISE;
+    in.block_w = 0;
+  }
+  return GSVD_OK;
+}
+
+// one problem with device pointers on stream s, workspace ws (>= P.total)
+int solve_device(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info, DevBuf& ws,
+                 unsigned long long* h_ctr, cudaStream_t s) {
+  Plan P;
+  if (!make_plan(cfg, p->dtype, p->m_f, p->m_g, p->n, P)) return GSVD_EINVAL;
+  CK(ws.ensure(P.total));
+  unsigned char* w = static_cast<unsigned char*>(ws.p);
+  cudaEvent_t e0, e1, e2;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventCreate(&e2);
+  cudaEventRecord(e0, s);
+  int* d_status = reinterpret_cast<int*>(w + P.off_status);
+  CK(cudaMemsetAsync(d_status, 0, 16, s));
+  // non-finite input check
+  CK(launch_check_finite(P.mf, P.n, P.cplx, (const double*)p->F, p->ldf, d_status + 1, s));
+  CK(launch_check_finite(P.mg, P.n, P.cplx, (const double*)p->G, p->ldg, d_status + 1, s));
+  int hst[4];
+  CK(cudaMemcpyAsync(hst, d_status, 16, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (hst[1]) {
+    info->status = GSVD_EINVAL;
+    return GSVD_EINVAL;
+  }
+  int status = GSVD_OK;
+  info->path = P.path;
+  info->block_w = P.path == GSVD_PATH_BLOCKED ? P.w : 0;
+  if (P.path == GSVD_PATH_POINTWISE) {
+    int idx0 = 0;
+    status = solve_pointwise(cfg, p, &idx0, 1, s, info);
+    if (status == GSVD_OK) status = info->status;
+  } else {
+    double* F = (double*)p->F;
+    double* G = (double*)p->G;
+    double* Z = (double*)p->Z;
+    double* zdiag = reinterpret_cast<double*>(w + P.off_zdiag);
+    std::vector<uint16_t> table = round_robin_table(P.neff);
+    CK(cudaMemcpyAsync(w + P.off_table, table.data(), table.size() * 2, cudaMemcpyHostToDevice, s));
+    CK(launch_prescale(P.mf, P.mg, P.n, P.cplx, F, p->ldf, G, p->ldg, Z, p->ldz, zdiag, d_status, s));
+    uint64_t tall = 0, tbig = 0;
+    int chol = 0, sw32 = 0, sw64 = 0;
+    if (cfg.precision == GSVD_PREC_MIXED) {
+      float* F32 = reinterpret_cast<float*>(w + P.off_f32);
+      float* G32 = reinterpret_cast<float*>(w + P.off_g32);
+      float* Z32 = reinterpret_cast<float*>(w + P.off_z32);
+      CK(launch_to_f32(P.mf, P.n, P.cplx, F, p->ldf, F32, P.mf, s));
+      CK(launch_to_f32(P.mg, P.n, P.cplx, G, p->ldg, G32, P.mg, s));
+      CK(launch_identity(P.n, P.cplx, true, Z32, P.n, s));
+      int st32 = run_sweeps(P, cfg, true, F32, P.mf, G32, P.mg, Z32, P.n, w, h_ctr, cfg.fp32_max_sweeps, s, &sw32,
+                            &tall, &tbig, &chol, info);
+      if (st32 != GSVD_OK && st32 != GSVD_ENOCONV) status = st32;
+      cudaEventRecord(e1, s);
+      // F <- F Z_acc, G <- G Z_acc (FP64), Z <- Z0 Z_acc
+      double* work = reinterpret_cast<double*>(w + P.off_work);
+      CK(launch_gemm_f64_by_f32(P.mf, P.n, P.cplx, F, p->ldf, Z32, P.n, work, P.mf, s));
+      CK(cudaMemcpy2DAsync(F, p->ldf * 8 * P.E, work, (size_t)P.mf * 8 * P.E, (size_t)P.mf * 8 * P.E, P.n,
+                           cudaMemcpyDeviceToDevice, s));
+      CK(launch_gemm_f64_by_f32(P.mg, P.n, P.cplx, G, p->ldg, Z32, P.n, work, P.mg, s));
+      CK(cudaMemcpy2DAsync(G, p->ldg * 8 * P.E, work, (size_t)P.mg * 8 * P.E, (size_t)P.mg * 8 * P.E, P.n,
+                           cudaMemcpyDeviceToDevice, s));
+      CK(launch_rowscale(P.n, P.cplx, zdiag, Z32, P.n, Z, p->ldz, s));
+    } else {
+      cudaEventRecord(e1, s);
+    }
+    if (status == GSVD_OK) {
+      status = run_sweeps(P, cfg, false, F, p->ldf, G, p->ldg, Z, p->ldz, w, h_ctr, cfg.max_sweeps, s, &sw64,
+                          &tall, &tbig, &chol, info);
+    }
+    CK(launch_finalize(P.mf, P.mg, P.n, P.cplx, F, p->ldf, G, p->ldg, Z, p->ldz, p->sigma_f, p->sigma_g, p->sigma,
+                       reinterpret_cast<double*>(w + P.off_norms), reinterpret_cast<int*>(w + P.off_rank),
+                       reinterpret_cast<double*>(w + P.off_work), d_status, s));
+    CK(cudaMemcpyAsync(hst, d_status, 16, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (status == GSVD_OK && hst[0] != 0) status = hst[0];
+    info->sweeps_fp32 = sw32;
+    info->sweeps_fp64 = sw64;
+    info->transf_all = tall;
+    info->transf_big = tbig;
+    info->chol_skipped = chol;
+  }
+  cudaEventRecord(e2, s);
+  cudaEventSynchronize(e2);
+  float ms_all = 0, ms_32 = 0, ms_64 = 0;
+  cudaEventElapsedTime(&ms_all, e0, e2);
+  if (P.path == GSVD_PATH_BLOCKED) {
+    cudaEventElapsedTime(&ms_32, e0, e1);
+    cudaEventElapsedTime(&ms_64, e1, e2);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaEventDestroy(e2);
+  info->t_total_us = ms_all * 1e3;
+  info->t_fp32_us = cfg.precision == GSVD_PREC_MIXED ? ms_32 * 1e3 : 0.0;
+  info->t_refine_us = cfg.precision == GSVD_PREC_MIXED ? ms_64 * 1e3 : 0.0;
+  info->status = status;
+  return status;
+}
+
+// host pointers: stage through device buffers (pinned or pageable host memory)
+int solve_host(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info, DevBuf& ws, unsigned long long* h_ctr,
+               cudaStream_t s) {
+  const int E = p->dtype == GSVD_C128 ? 2 : 1;
+  const size_t es = 8 * E;
+  const size_t bF = align256((size_t)p->m_f * p->n * es), bG = align256((size_t)p->m_g * p->n * es),
+               bZ = align256((size_t)p->n * p->n * es), bv = align256((size_t)p->n * 8);
+  DevBuf stage;
+  CK(stage.ensure(bF + bG + bZ + 3 * bv));
+  unsigned char* b = static_cast<unsigned char*>(stage.p);
+  gsvd_problem d = *p;
+  d.F = b; d.ldf = p->m_f;
+  d.G = b + bF; d.ldg = p->m_g;
+  d.Z = b + bF + bG; d.ldz = p->n;
+  d.sigma_f = reinterpret_cast<double*>(b + bF + bG + bZ);
+  d.sigma_g = reinterpret_cast<double*>(b + bF + bG + bZ + bv);
+  d.sigma = reinterpret_cast<double*>(b + bF + bG + bZ + 2 * bv);
+  CK(cudaMemcpy2DAsync(d.F, p->m_f * es, p->F, p->ldf * es, p->m_f * es, p->n, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpy2DAsync(d.G, p->m_g * es, p->G, p->ldg * es, p->m_g * es, p->n, cudaMemcpyHostToDevice, s));
+  int st = solve_device(cfg, &d, info, ws, h_ctr, s);
+  if (st == GSVD_EINVAL && info->status == GSVD_EINVAL) return st;
+  CK(cudaMemcpy2DAsync(p->F, p->ldf * es, d.F, p->m_f * es, p->m_f * es, p->n, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpy2DAsync(p->G, p->ldg * es, d.G, p->m_g * es, p->m_g * es, p->n, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpy2DAsync(p->Z, p->ldz * es, d.Z, p->n * es, p->n * es, p->n, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(p->sigma_f, d.sigma_f, p->n * 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(p->sigma_g, d.sigma_g, p->n * 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(p->sigma, d.sigma, p->n * 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return st;
+}
+
+int solve_any(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info, DevBuf& ws, unsigned long long* h_ctr,
+              cudaStream_t s) {
+  int v = validate(p);
+  if (v != GSVD_OK) {
+    info->status = v;
+    return v;
+  }
+  const bool dev = is_device_ptr(p->F);
+  if (dev != is_device_ptr(p->G) || dev != is_device_ptr(p->Z) || dev != is_device_ptr(p->sigma)) {
+    info->status = GSVD_EINVAL;
+    return GSVD_EINVAL;
+  }
+  return dev ? solve_device(cfg, p, info, ws, h_ctr, s) : solve_host(cfg, p, info, ws, h_ctr, s);
+}
+
+void worker_loop(gsvd_ctx* h) {
+  cudaStream_t s;
+  cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  DevBuf ws;
+  unsigned long long* h_ctr = nullptr;
+  cudaMallocHost(&h_ctr, NCTR * sizeof(unsigned long long));
+  for (;;) {
+    Request* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(h->mu);
+      // continuous admission: the oldest queued request starts as soon as the
+      // memory budget (and this free worker) allow it
+      h->cv.wait(lk, [&] {
+        if (h->stop) return true;
+        if (h->queue.empty()) return false;
+        Request* q = h->reqs[h->queue.front()].get();
+        return h->used_bytes + q->bytes <= h->cfg.hbm_budget_bytes || h->inflight == 0;
+      });
+      if (h->stop && h->queue.empty()) break;
+      if (h->queue.empty()) continue;
+      const uint64_t t = h->queue.front();
+      h->queue.pop_front();
+      r = h->reqs[t].get();
+      r->state = 1;
+      h->used_bytes += r->bytes;
+      ++h->inflight;
+    }
+    gsvd_info info;
+    std::memset(&info, 0, sizeof info);
+    solve_device(h->cfg, &r->prob, &info, ws, h_ctr, s);
+    {
+      std::lock_guard<std::mutex> lk(h->mu);
+      r->info = info;
+      r->state = 2;
+      h->used_bytes -= r->bytes;
+      --h->inflight;
+    }
+    h->cv.notify_all();
+  }
+  cudaFreeHost(h_ctr);
+  cudaStreamDestroy(s);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------- ABI ----
+extern "C" {
+
+void gsvd_config_default(gsvd_config* c) {
+  std::memset(c, 0, sizeof *c);
+  c->precision = GSVD_PREC_FP64;
+  c->block_w = 0;
+  c->max_sweeps = 30;
+  c->inner_max_sweeps = 30;
+  c->criterion = 1;
+  c->sort = 1;
+  c->path = GSVD_PATH_AUTO;
+  c->order = GSVD_ORDER_ROUND_ROBIN;
+  c->fp32_max_sweeps = 30;
+  c->timeout_ms = 0;
+  c->hbm_budget_bytes = 60ull << 30;
+  c->max_inflight = 16;
+  c->profile = 0;
+  c->inner_max_sweeps_fp32 = 1;
+}
+
+int gsvd_create(gsvd_handle* h, const gsvd_config* cfg, void* stream) {
+  if (!h) return GSVD_EINVAL;
+  gsvd_ctx* c = new (std::nothrow) gsvd_ctx;
+  if (!c) return GSVD_ENOMEM;
+  if (cfg)
+    c->cfg = *cfg;
+  else
+    gsvd_config_default(&c->cfg);
+  if (c->cfg.max_sweeps < 1 || c->cfg.inner_max_sweeps < 1 || c->cfg.fp32_max_sweeps < 0 ||
+      (c->cfg.criterion != 1 && c->cfg.criterion != 2) || c->cfg.max_inflight < 1 ||
+      (c->cfg.precision != GSVD_PREC_FP64 && c->cfg.precision != GSVD_PREC_MIXED)) {
+    delete c;
+    return GSVD_EINVAL;
+  }
+  c->stream = static_cast<cudaStream_t>(stream);
+  *h = c;
+  return GSVD_OK;
+}
+
+int gsvd_destroy(gsvd_handle h) {
+  if (!h) return GSVD_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(h->mu);
+    h->stop = true;
+  }
+  h->cv.notify_all();
+  for (auto& t : h->workers) t.join();
+  if (h->h_ctr) cudaFreeHost(h->h_ctr);
+  delete h;
+  return GSVD_OK;
+}
+
+static int ensure_pinned(gsvd_handle h) {
+  if (h->h_ctr) return GSVD_OK;
+  return cudaMallocHost(&h->h_ctr, NCTR * sizeof(unsigned long long)) == cudaSuccess ? GSVD_OK : GSVD_ECUDA;
+}
+
+int gsvd_solve(gsvd_handle h, const gsvd_problem* p, gsvd_info* info) {
+  if (!h) return GSVD_EINVAL;
+  gsvd_info tmp;
+  std::memset(&tmp, 0, sizeof tmp);
+  int v = validate(p);
+  if (v != GSVD_OK) {
+    if (info) { *info = tmp; info->status = v; }
+    return v;
+  }
+  int pe = ensure_pinned(h);
+  if (pe != GSVD_OK) return pe;
+  int st = solve_any(h->cfg, p, &tmp, h->ws, h->h_ctr, h->stream);
+  if (info) *info = tmp;
+  return st;
+}
+
+int gsvd_solve_batched(gsvd_handle h, const gsvd_problem* ps, int32_t count, gsvd_info* infos) {
+  if (!h || count < 0 || (count > 0 && !ps)) return GSVD_EINVAL;
+  if (count == 0) return GSVD_OK;
+  int pe = ensure_pinned(h);
+  if (pe != GSVD_OK) return pe;
+  std::vector<gsvd_info> loc(count);
+  std::memset(loc.data(), 0, sizeof(gsvd_info) * count);
+  std::vector<int> pw, blk;
+  for (int k = 0; k < count; ++k) {
+    int v = validate(&ps[k]);
+    if (v == GSVD_OK && !(is_device_ptr(ps[k].F) && is_device_ptr(ps[k].G) && is_device_ptr(ps[k].Z)))
+      v = GSVD_EINVAL;
+    if (v != GSVD_OK) {
+      loc[k].status = v;
+      continue;
+    }
+    Plan P;
+    if (!make_plan(h->cfg, ps[k].dtype, ps[k].m_f, ps[k].m_g, ps[k].n, P)) {
+      loc[k].status = GSVD_EINVAL;
+      continue;
+    }
+    (P.path == GSVD_PATH_POINTWISE ? pw : blk).push_back(k);
+  }
+  int first = GSVD_OK;
+  if (!pw.empty()) {
+    int st = solve_pointwise(h->cfg, ps, pw.data(), (int)pw.size(), h->stream, loc.data());
+    if (st != GSVD_OK)
+      for (int k : pw) loc[k].status = st;
+  }
+  for (int k : blk) solve_device(h->cfg, &ps[k], &loc[k], h->ws, h->h_ctr, h->stream);
+  for (int k = 0; k < count; ++k)
+    if (loc[k].status != GSVD_OK && first == GSVD_OK) first = loc[k].status;
+  if (infos) std::memcpy(infos, loc.data(), sizeof(gsvd_info) * count);
+  return first;
+}
+
+uint64_t gsvd_workspace_bytes(const gsvd_config* cfg, int32_t dtype, int64_t mf, int64_t mg, int64_t n) {
+  gsvd_config c;
+  if (cfg)
+    c = *cfg;
+  else
+    gsvd_config_default(&c);
+  Plan P;
+  if (!make_plan(c, dtype, mf, mg, n, P)) return 0;
+  return P.total;
+}
+
+int gsvd_submit(gsvd_handle h, const gsvd_problem* p, uint64_t* ticket) {
+  if (!h || !ticket) return GSVD_EINVAL;
+  int v = validate(p);
+  if (v != GSVD_OK) return v;
+  if (!(is_device_ptr(p->F) && is_device_ptr(p->G) && is_device_ptr(p->Z))) return GSVD_EINVAL;
+  Plan P;
+  if (!make_plan(h->cfg, p->dtype, p->m_f, p->m_g, p->n, P)) return GSVD_EINVAL;
+  const uint64_t bytes = P.total;
+  if (bytes > h->cfg.hbm_budget_bytes) return GSVD_ETOOBIG;
+  std::unique_ptr<Request> r(new Request);
+  r->prob = *p;
+  std::memset(&r->info, 0, sizeof r->info);
+  r->bytes = bytes;
+  r->state = 0;
+  {
+    std::lock_guard<std::mutex> lk(h->mu);
+    if (h->workers.empty())
+      for (int k = 0; k < h->cfg.max_inflight; ++k) h->workers.emplace_back(worker_loop, h);
+    *ticket = h->next_ticket++;
+    h->reqs[*ticket] = std::move(r);
+    h->queue.push_back(*ticket);
+  }
+  h->cv.notify_all();
+  return GSVD_OK;
+}
+
+int gsvd_poll(gsvd_handle h, uint64_t ticket, gsvd_info* info) {
+  if (!h) return GSVD_EINVAL;
+  std::lock_guard<std::mutex> lk(h->mu);
+  auto it = h->reqs.find(ticket);
+  if (it == h->reqs.end()) return GSVD_EINVAL;
+  if (it->second->state != 2) return GSVD_EAGAIN;
+  const int st = it->second->info.status;
+  if (info) *info = it->second->info;
+  h->reqs.erase(it);
+  return st;
+}
+
+const char* gsvd_strerror(int s) {
+  switch (s) {
+    case GSVD_OK: return "ok";
+    case GSVD_EAGAIN: return "not finished";
+    case GSVD_EINVAL: return "invalid argument";
+    case GSVD_ENOMEM: return "out of device memory";
+    case GSVD_ENOCONV: return "sweep cap reached without convergence";
+    case GSVD_ENOTPD: return "pivot block not positive definite (G rank deficient)";
+    case GSVD_EOVERFLOW: return "non-finite column norm";
+    case GSVD_ETIMEOUT: return "timed out";
+    case GSVD_ECUDA: return "CUDA runtime error";
+    case GSVD_ETOOBIG: return "request exceeds the memory budget";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

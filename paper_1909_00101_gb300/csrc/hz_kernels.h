@@ -1,0 +1,121 @@
+// hz_kernels.h -- internal interface between the host runtime (gsvd_api.cu)
+// and the CUDA kernels.  Not part of the public C ABI (include/gsvd.h).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hz {
+
+// ---------------------------------------------------------- pointwise ----
+struct PwStats {
+  int32_t status;
+  int32_t sweeps;
+  long long transf_all;
+  long long transf_big;
+};
+
+struct PwProblem {
+  void* F;
+  long long ldf;
+  void* G;
+  long long ldg;
+  void* Z;
+  long long ldz;
+  int mf, mg, n, pad;
+  double* sigma_f;
+  double* sigma_g;
+  double* sigma;
+  PwStats* stats;
+};
+
+struct PwParams {
+  double eps;
+  int max_sweeps;
+  bool sort;
+  bool f32cls;
+  bool crit2;
+  bool rowcyc;  // row-cyclic wavefront order (else round robin)
+};
+
+size_t pointwise_smem_bytes(int mf, int mg, int n, bool cplx, bool fp32, int slots);
+// slots: the largest number of pairs per step over the batch (shared-memory layout)
+cudaError_t launch_pointwise(const PwProblem* d_probs, int count, int slots, bool cplx, bool fp32, size_t smem,
+                             const PwParams& prm, cudaStream_t stream);
+
+// ------------------------------------------------------------ blocked ----
+// One solve (or one member of a batch) on the blocked path.  Matrices are
+// column-major; complex data interleaved (re, im).  T is double (FP64 sweeps)
+// or float (FP32 bulk sweeps of the mixed-precision path).
+struct BlkDims {
+  int mf, mg, n;
+  int w;        // block width; block k covers columns [k w, min((k+1) w, n))
+  int nblk;     // N = ceil(n / w)
+  int nslots;   // pairs per outer step = N_eff / 2 (N_eff = N rounded up to even)
+  int rf, rg;   // row splits of the Gram over F and G
+  int trows;    // rows per Gram row split are a multiple of this
+};
+
+struct BlkBuffers {
+  void* F;
+  long long ldf;
+  void* G;
+  long long ldg;
+  void* Z;
+  long long ldz;
+  void* partial;              // [nslots][rf+rg][V][V] of T
+  void* ztil;                 // [nslots][V][V] of T (real view of Z-tilde)
+  int* flags;                 // [nslots]: 1 = apply needed
+  unsigned long long* ctr;    // [0] all, [1] big, [2] failures (ENOTPD), [3] chol failures skipped,
+                              // [4] visits, [5] visits applied
+  const uint16_t* table;      // outer table [N_eff - 1][nslots][2]
+};
+
+struct InnerParams {
+  double eps;          // unit roundoff of the sweep's data type
+  double tol;          // > 0: skip-test threshold to use instead of eps * sqrt(columns)
+  int inner_max;       // inner sweeps cap (30 = FB, 1 = BO)
+  bool sort;
+  bool f32cls;         // classify small/big at FP32 resolution
+  bool crit2;
+  bool chol_skip;      // Cholesky failure: skip the visit (FP32 bulk) instead of failing
+};
+
+int blk_vmax(int w, bool cplx);  // real-view width V of the kernels for this w
+cudaError_t launch_gram(const BlkDims& d, const BlkBuffers& b, bool cplx, bool fp32, int step,
+                        cudaStream_t s);
+cudaError_t launch_inner(const BlkDims& d, const BlkBuffers& b, bool cplx, bool fp32, int step,
+                         const InnerParams& p, cudaStream_t s);
+cudaError_t launch_apply(const BlkDims& d, const BlkBuffers& b, bool cplx, bool fp32, int step,
+                         cudaStream_t s);
+
+// -------------------------------------------------- column operations ----
+// prescale: z_j = 1/||g_j||, F <- F Z0, G <- G Z0, Z <- Z0 (FP64, in place)
+cudaError_t launch_prescale(int mf, int mg, int n, bool cplx, double* F, long long ldf, double* G,
+                            long long ldg, double* Z, long long ldz, double* zdiag, int* status,
+                            cudaStream_t s);
+// between sweeps: f_j, g_j, z_j *= (||f_j||^2 + ||g_j||^2)^{-1/2} (T = double or float)
+cudaError_t launch_rescale(int mf, int mg, int n, bool cplx, bool fp32, void* F, long long ldf, void* G,
+                           long long ldg, void* Z, long long ldz, cudaStream_t s);
+// final: norms, Theta, Sigma, rank sort, gather into U, V, Z (work: scratch of
+// max(mf, mg, n) * n elements), sigma vectors.
+cudaError_t launch_finalize(int mf, int mg, int n, bool cplx, double* F, long long ldf, double* G,
+                            long long ldg, double* Z, long long ldz, double* sf, double* sg,
+                            double* sigma, double* norms, int* rank, double* work, int* status,
+                            cudaStream_t s);
+// conversions for the mixed-precision path
+cudaError_t launch_to_f32(int m, int n, bool cplx, const double* src, long long lds, float* dst,
+                          long long ldd, cudaStream_t s);
+cudaError_t launch_identity(int n, bool cplx, bool fp32, void* Z, long long ldz, cudaStream_t s);
+// C (m x n) = A (m x n, FP64) * B (n x n, FP32 widened to FP64), dst may not alias A.
+cudaError_t launch_gemm_f64_by_f32(int m, int n, bool cplx, const double* A, long long lda,
+                                   const float* B, long long ldb, double* C, long long ldc,
+                                   cudaStream_t s);
+// Z64 = diag(zdiag) * Z32 (rows scaled), FP64 result
+cudaError_t launch_rowscale(int n, bool cplx, const double* zdiag, const float* Z32, long long ld32,
+                            double* Z, long long ldz, cudaStream_t s);
+// non-finite check of a column-major matrix: sets *flag = 1 on NaN/Inf
+cudaError_t launch_check_finite(int m, int n, bool cplx, const double* A, long long lda, int* flag,
+                                cudaStream_t s);
+
+}  // namespace hz

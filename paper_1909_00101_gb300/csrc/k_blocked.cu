@@ -1,0 +1,744 @@
+// k_blocked.cu -- one outer step of the blocked one-sided implicit
+// Hari-Zimmermann GSVD (Sec. 2.3-2.5 of arXiv 1909.00101), re-designed for
+// sm_103a as three kernels per step instead of the paper's one fused kernel:
+//
+//   k_gram   grid (pair, row split): partial pivot Grams A-hat = [F_p F_q]^* [F_p F_q]
+//            and B-hat = [G_p G_q]^* [G_p G_q] over a slab of rows (FP64: DMMA
+//            m8n8k4 on the tensor pipe; FP32: FFMA with register tiles).
+//   k_inner  grid (pair): fixed-order sum of the partials, Cholesky of A-hat and
+//            B-hat (FP64), then the pointwise implicit HZ on (F-hat, G-hat) in
+//            shared memory with FP64 2x2 parameters one pair per lane, and the
+//            Theta-tilde rescaling that gives Z-tilde = Z-hat Theta-tilde.
+//   k_apply  grid (pair, row tile): [Y_p Y_q] <- [Y_p Y_q] Z-tilde in place for
+//            Y = F, G, Z (FP64: DMMA; FP32: FFMA).
+//
+// Splitting the row dimension of the Gram and the apply over many CTAs fills
+// the 152 SMs even when a step has few block pairs (the paper's one CTA per
+// pair leaves most SMs idle for n = 2048).  Complex data is handled by real
+// views: with W = [Re Y, Im Y], Re(Y^*Y) and Im(Y^*Y) are sums and differences
+// of blocks of W^T W, and Y Z = [Re Y, Im Y] [[Re Z, Im Z], [-Im Z, Re Z]].
+#include <type_traits>
+
+#include "hz_device.cuh"
+#include "hz_kernels.h"
+
+namespace hz {
+
+namespace {
+
+constexpr int TR = 64;  // rows per tile of the Gram and the apply
+
+__device__ __forceinline__ void dmma884(double& c0, double& c1, double a, double b) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+               : "+d"(c0), "+d"(c1)
+               : "d"(a), "d"(b));
+}
+
+struct PairCols {
+  int cp, wp, cq, wq, bb;
+  __device__ __forceinline__ int gcol(int c) const { return c < wp ? cp + c : cq + (c - wp); }
+};
+
+__device__ __forceinline__ bool load_pair(const BlkDims& d, const BlkBuffers& b, int step, int slot,
+                                          PairCols& pc) {
+  const uint16_t* pr = b.table + ((size_t)step * d.nslots + slot) * 2;
+  const int p = pr[0], q = pr[1];
+  if (p >= d.nblk || q >= d.nblk) return false;
+  pc.cp = p * d.w;
+  pc.wp = min(d.w, d.n - pc.cp);
+  pc.cq = q * d.w;
+  pc.wq = min(d.w, d.n - pc.cq);
+  pc.bb = pc.wp + pc.wq;
+  return true;
+}
+
+// Load rows [r0, r0+TR) of the real view of [Y_p Y_q] (zero outside) into
+// shared memory: column-major (Ws[c * ld + r]) or row-major (Ws[r * ld + c]).
+template <class T, bool CPLX, bool COLMAJ>
+__device__ __forceinline__ void load_tile(T* Ws, int ld, const T* Y, long long ldy, int m, int r0,
+                                          const PairCols& pc, int V) {
+  if constexpr (!CPLX) {
+    for (int idx = threadIdx.x; idx < V * TR; idx += blockDim.x) {
+      const int c = idx / TR, r = idx % TR;
+      T v = T(0);
+      if (c < pc.bb && r0 + r < m) v = Y[(size_t)pc.gcol(c) * ldy + r0 + r];
+      if (COLMAJ) Ws[c * ld + r] = v; else Ws[r * ld + c] = v;
+    }
+  } else {
+    using T2 = typename std::conditional<std::is_same<T, double>::value, double2, float2>::type;
+    const T2* Y2 = reinterpret_cast<const T2*>(Y);
+    for (int idx = threadIdx.x; idx < (V / 2) * TR; idx += blockDim.x) {
+      const int c = idx / TR, r = idx % TR;
+      T re = T(0), im = T(0);
+      if (c < pc.bb && r0 + r < m) {
+        const T2 v = Y2[(size_t)pc.gcol(c) * ldy + r0 + r];
+        re = v.x;
+        im = v.y;
+      }
+      // real view: column c is Re, column bb + c is Im; for c >= bb the two
+      // zero padding columns 2c and 2c + 1 (together they cover [2 bb, V))
+      const int cr = (c < pc.bb) ? c : 2 * c;
+      const int ci = (c < pc.bb) ? pc.bb + c : 2 * c + 1;
+      if (COLMAJ) {
+        Ws[cr * ld + r] = re;
+        Ws[ci * ld + r] = im;
+      } else {
+        Ws[r * ld + cr] = re;
+        Ws[r * ld + ci] = im;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- Gram ----
+// FP64: one warp per upper-triangle 8x8 tile of the V x V Gram (DMMA m8n8k4),
+// so the tiles (3, 10 or 36 for V = 16, 32, 64) are balanced over the warps.
+template <class T, int V>
+__host__ __device__ constexpr int gram_threads() {
+  return std::is_same<T, double>::value ? 32 * ((V / 8) * (V / 8 + 1) / 2 > 16 ? ((V / 8) * (V / 8 + 1) / 2 + 2) / 3
+                                                                                : (V / 8) * (V / 8 + 1) / 2)
+                                        : 256;
+}
+
+template <class T, bool CPLX, int V>
+__global__ void __launch_bounds__(gram_threads<T, V>()) k_gram(BlkDims d, BlkBuffers b, int step) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ws = reinterpret_cast<T*>(smem_raw);
+  const int slot = blockIdx.x, s = blockIdx.y;
+  PairCols pc;
+  if (!load_pair(d, b, step, slot, pc)) return;
+  const bool isF = s < d.rf;
+  const int m = isF ? d.mf : d.mg;
+  const int nsplit = isF ? d.rf : d.rg;
+  const int si = isF ? s : s - d.rf;
+  const int per = ((m + nsplit - 1) / nsplit + TR - 1) / TR * TR;
+  const int r0 = si * per, r1 = min(m, r0 + per);
+  const T* Y = static_cast<const T*>(isF ? b.F : b.G);
+  const long long ld = isF ? b.ldf : b.ldg;
+  T* out = static_cast<T*>(b.partial) + ((size_t)slot * (d.rf + d.rg) + s) * V * V;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  if constexpr (std::is_same<T, double>::value) {
+    constexpr int LDT = TR + 4;
+    constexpr int NB = V / 8;
+    constexpr int NT = NB * (NB + 1) / 2;  // upper-triangle 8x8 tiles
+    constexpr int NW = gram_threads<T, V>() / 32;
+    constexpr int PER = (NT + NW - 1) / NW;  // tiles per warp
+    double acc[PER][2];
+    int ti[PER], tj[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      acc[u][0] = acc[u][1] = 0.0;
+      int t = warp + NW * u, a = 0;
+      ti[u] = -1;
+      tj[u] = 0;
+      if (t < NT) {
+        while (t >= NB - a) { t -= NB - a; ++a; }
+        ti[u] = a;
+        tj[u] = a + t;
+      }
+    }
+    for (int rt = r0; rt < r1; rt += TR) {
+      load_tile<T, CPLX, true>(Ws, LDT, Y, ld, r1, rt, pc, V);
+      __syncthreads();
+#pragma unroll 4
+      for (int k0 = 0; k0 < TR; k0 += 4) {
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+          if (ti[u] < 0) continue;
+          const double a = Ws[(ti[u] * 8 + (lane >> 2)) * LDT + k0 + (lane & 3)];
+          const double bv = Ws[(tj[u] * 8 + (lane >> 2)) * LDT + k0 + (lane & 3)];
+          dmma884(acc[u][0], acc[u][1], a, bv);
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      if (ti[u] < 0) continue;
+      const int i = ti[u] * 8 + (lane >> 2), j = tj[u] * 8 + 2 * (lane & 3);
+      out[i * V + j] = acc[u][0];
+      out[i * V + j + 1] = acc[u][1];
+    }
+  } else {
+    constexpr int LDT = V + 1;
+    constexpr int NV = V / 16;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float acc[NV][NV];
+#pragma unroll
+    for (int u = 0; u < NV; ++u)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[u][v] = 0.0f;
+    for (int rt = r0; rt < r1; rt += TR) {
+      load_tile<T, CPLX, false>(Ws, LDT, Y, ld, r1, rt, pc, V);
+      __syncthreads();
+#pragma unroll 4
+      for (int r = 0; r < TR; ++r) {
+        float a[NV], bv[NV];
+#pragma unroll
+        for (int u = 0; u < NV; ++u) a[u] = Ws[r * LDT + tx + 16 * u];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) bv[v] = Ws[r * LDT + ty + 16 * v];
+#pragma unroll
+        for (int u = 0; u < NV; ++u)
+#pragma unroll
+          for (int v = 0; v < NV; ++v) acc[u][v] = fmaf(a[u], bv[v], acc[u][v]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < NV; ++u)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) out[(tx + 16 * u) * V + ty + 16 * v] = acc[u][v];
+  }
+}
+
+// --------------------------------------------------------------- inner ----
+struct PivIn {
+  double a11, a22, ar, ai, br, bi;
+};
+
+// Ti: data type of the inner sweeps (double, or float in FP32 bulk sweeps);
+// To: type of the outer data (partials and Z-tilde).
+template <class Ti, class To, bool CPLX, int V>
+__global__ void __launch_bounds__(512) k_inner(BlkDims d, BlkBuffers b, int step, InnerParams prm) {
+  constexpr int E = CPLX ? 2 : 1;
+  constexpr int BMAX = CPLX ? V / 2 : V;  // max columns of the pair
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* A = reinterpret_cast<double*>(smem_raw);        // E * BMAX * BMAX
+  double* Bm = A + E * BMAX * BMAX;                       // E * BMAX * BMAX
+  Ti* Zh = reinterpret_cast<Ti*>(Bm + E * BMAX * BMAX);   // E * BMAX * BMAX
+  PivIn* pin = reinterpret_cast<PivIn*>(Zh + E * BMAX * BMAX);
+  PivotOut* pout = reinterpret_cast<PivotOut*>(pin + BMAX / 2 + 1);
+  __shared__ int s_ctr[4];  // all, big, fail, any-change
+  __shared__ double s_inv;
+  __shared__ int s_bad;
+
+  const int slot = blockIdx.x;
+  PairCols pc;
+  if (!load_pair(d, b, step, slot, pc)) return;
+  const int bb = pc.bb;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int S = d.rf + d.rg;
+  const To* P = static_cast<const To*>(b.partial) + (size_t)slot * S * V * V;
+  if (threadIdx.x < 4) s_ctr[threadIdx.x] = 0;
+  if (threadIdx.x == 0) {
+    s_bad = 0;
+    atomicAdd(&b.ctr[4], 1ull);
+  }
+
+  // 1. fixed-order sum of the partials into A-hat and B-hat (column-major,
+  //    upper triangle, FP64), then the conjugate mirror.
+  for (int idx = threadIdx.x; idx < bb * bb; idx += blockDim.x) {
+    const int j = idx / bb, i = idx % bb;
+    if (i > j) continue;
+    for (int mat = 0; mat < 2; ++mat) {
+      const int s0 = mat ? d.rf : 0, s1 = mat ? S : d.rf;
+      double* M = mat ? Bm : A;
+      double re = 0.0, im = 0.0;
+      for (int s = s0; s < s1; ++s) {
+        const To* Q = P + (size_t)s * V * V;
+        if constexpr (!CPLX) {
+          re += (double)Q[i * V + j];
+        } else {
+          re += (double)Q[i * V + j] + (double)Q[(bb + i) * V + bb + j];
+          im += (double)Q[i * V + bb + j] - (double)Q[j * V + bb + i];
+        }
+      }
+      if constexpr (!CPLX) {
+        M[j * BMAX + i] = re;
+        M[i * BMAX + j] = re;
+      } else {
+        M[2 * (j * BMAX + i)] = re;
+        M[2 * (j * BMAX + i) + 1] = (i == j) ? 0.0 : im;
+        M[2 * (i * BMAX + j)] = re;
+        M[2 * (i * BMAX + j) + 1] = (i == j) ? 0.0 : -im;
+      }
+    }
+  }
+  __syncthreads();
+
+  // 2. Cholesky A-hat = R^* R (upper R), then B-hat, in FP64; strict lower
+  //    triangle zeroed.  A non-positive pivot fails the visit.
+  for (int mat = 0; mat < 2; ++mat) {
+    double* M = mat ? Bm : A;
+    for (int k = 0; k < bb; ++k) {
+      if (threadIdx.x == 0) {
+        const double dkk = M[E * (k * BMAX + k)];
+        if (!(dkk > 0.0) || !isfinite(dkk)) {
+          s_bad = 1;
+          s_inv = 0.0;
+        } else {
+          const double r = sqrt(dkk);
+          M[E * (k * BMAX + k)] = r;
+          s_inv = 1.0 / r;
+        }
+      }
+      __syncthreads();
+      if (s_bad) break;
+      const double inv = s_inv;
+      for (int j = k + 1 + threadIdx.x; j < bb; j += blockDim.x) {
+        M[E * (j * BMAX + k)] *= inv;
+        if constexpr (CPLX) M[E * (j * BMAX + k) + 1] *= inv;
+      }
+      __syncthreads();
+      const int rem = bb - k - 1;
+      for (int idx = threadIdx.x; idx < rem * rem; idx += blockDim.x) {
+        const int j = k + 1 + idx / rem, i = k + 1 + idx % rem;
+        if (i > j) continue;
+        if constexpr (!CPLX) {
+          M[j * BMAX + i] = fma(-M[i * BMAX + k], M[j * BMAX + k], M[j * BMAX + i]);
+        } else {
+          // M_ij -= conj(R_ki) R_kj
+          const double kir = M[2 * (i * BMAX + k)], kii = M[2 * (i * BMAX + k) + 1];
+          const double kjr = M[2 * (j * BMAX + k)], kji = M[2 * (j * BMAX + k) + 1];
+          M[2 * (j * BMAX + i)] -= kir * kjr + kii * kji;
+          M[2 * (j * BMAX + i) + 1] -= kir * kji - kii * kjr;
+        }
+      }
+      __syncthreads();
+    }
+    if (s_bad) break;
+  }
+  if (s_bad) {
+    if (threadIdx.x == 0) {
+      b.flags[slot] = 0;
+      atomicAdd(&b.ctr[prm.chol_skip ? 3 : 2], 1ull);
+    }
+    return;
+  }
+
+  // 3. F-hat, G-hat (inner data type, in place), Z-hat = I
+  {
+    double tmpA[E * BMAX * BMAX / 512 + 1], tmpB[E * BMAX * BMAX / 512 + 1];
+    int cnt = 0;
+    for (int idx = threadIdx.x; idx < E * bb * bb; idx += blockDim.x, ++cnt) {
+      const int j = idx / (E * bb), i = (idx % (E * bb)) / E, part = idx % E;
+      const bool low = i > j;
+      tmpA[cnt] = low ? 0.0 : A[E * (j * BMAX + i) + part];
+      tmpB[cnt] = low ? 0.0 : Bm[E * (j * BMAX + i) + part];
+    }
+    __syncthreads();
+    Ti* Fh = reinterpret_cast<Ti*>(A);
+    Ti* Gh = reinterpret_cast<Ti*>(Bm);
+    cnt = 0;
+    for (int idx = threadIdx.x; idx < E * bb * bb; idx += blockDim.x, ++cnt) {
+      Fh[idx] = static_cast<Ti>(tmpA[cnt]);
+      Gh[idx] = static_cast<Ti>(tmpB[cnt]);
+      Zh[idx] = Ti(0);
+    }
+    __syncthreads();
+  }
+  Ti* Fh = reinterpret_cast<Ti*>(A);  // bb x bb, ld bb (E scalars per element)
+  Ti* Gh = reinterpret_cast<Ti*>(Bm);
+
+  // 4. inner prescale (variant 0): z_j = 1/||g-hat_j||
+  for (int j = warp; j < bb; j += nwarps) {
+    Ti s = Ti(0);
+    for (int r = lane; r < E * bb; r += 32) {
+      const Ti v = Gh[j * E * bb + r];
+      s += v * v;
+    }
+    s = warp_sum(s);
+    const Ti zj = Ti(1) / sqrt(s);
+    for (int r = lane; r < E * bb; r += 32) {
+      Fh[j * E * bb + r] *= zj;
+      Gh[j * E * bb + r] *= zj;
+    }
+    if (lane == 0) Zh[j * E * bb + E * j] = zj;
+  }
+  __syncthreads();
+
+  const int M = bb + (bb & 1);
+  const int npairs = M / 2;
+  const double tol = prm.tol > 0.0 ? prm.tol : prm.eps * sqrt((double)bb);
+  for (int sw = 0; sw < prm.inner_max; ++sw) {
+    int sweep_all = 0;
+    for (int st = 0; st < M - 1; ++st) {
+      for (int k = warp; k < npairs; k += nwarps) {
+        int i, j;
+        rr_pair(M, st, k, i, j);
+        if (j >= bb) continue;
+        Ti v[4] = {Ti(0), Ti(0), Ti(0), Ti(0)};
+        Ti w2[2] = {Ti(0), Ti(0)};
+        if constexpr (!CPLX) {
+          for (int r = lane; r < bb; r += 32) {
+            const Ti fi = Fh[i * bb + r], fj = Fh[j * bb + r];
+            v[0] += fi * fi;
+            v[1] += fj * fj;
+            v[2] += fi * fj;
+            v[3] += Gh[i * bb + r] * Gh[j * bb + r];
+          }
+          warp_sum4(v);
+        } else {
+          for (int r = lane; r < bb; r += 32) {
+            const Ti fir = Fh[2 * (i * bb + r)], fii = Fh[2 * (i * bb + r) + 1];
+            const Ti fjr = Fh[2 * (j * bb + r)], fji = Fh[2 * (j * bb + r) + 1];
+            const Ti gir = Gh[2 * (i * bb + r)], gii = Gh[2 * (i * bb + r) + 1];
+            const Ti gjr = Gh[2 * (j * bb + r)], gji = Gh[2 * (j * bb + r) + 1];
+            v[0] += fir * fir + fii * fii;
+            v[1] += fjr * fjr + fji * fji;
+            v[2] += fir * fjr + fii * fji;
+            v[3] += fir * fji - fii * fjr;
+            w2[0] += gir * gjr + gii * gji;
+            w2[1] += gir * gji - gii * gjr;
+          }
+          warp_sum4(v);
+          w2[0] = warp_sum(w2[0]);
+          w2[1] = warp_sum(w2[1]);
+        }
+        if (lane == 0) {
+          PivIn p;
+          p.a11 = v[0]; p.a22 = v[1]; p.ar = v[2];
+          if constexpr (CPLX) { p.ai = v[3]; p.br = w2[0]; p.bi = w2[1]; }
+          else { p.ai = 0.0; p.br = v[3]; p.bi = 0.0; }
+          pin[k] = p;
+        }
+      }
+      __syncthreads();
+      // FP64 parameters, one pair per lane of warp 0 (npairs <= 32)
+      if (warp == 0 && lane < npairs) {
+        int i, j;
+        rr_pair(M, st, lane, i, j);
+        if (j < bb) {
+          const PivIn p = pin[lane];
+          PivotOut o;
+          if constexpr (CPLX)
+            o = pivot_cplx(p.a11, p.a22, p.ar, p.ai, p.br, p.bi, tol, prm.sort, prm.f32cls, prm.crit2);
+          else
+            o = pivot_real(p.a11, p.a22, p.ar, p.br, tol, prm.sort, prm.f32cls, prm.crit2);
+          pout[lane] = o;
+          if (o.flags & PV_ROT) atomicAdd(&s_ctr[0], 1);
+          if (o.flags & PV_BIG) atomicAdd(&s_ctr[1], 1);
+          if (o.flags & PV_FAIL) atomicOr(&s_ctr[2], 1);
+          if (o.flags & (PV_ROT | PV_SWAP)) atomicOr(&s_ctr[3], 1);
+        }
+      }
+      __syncthreads();
+      for (int k = warp; k < npairs; k += nwarps) {
+        int i, j;
+        rr_pair(M, st, k, i, j);
+        if (j >= bb) continue;
+        const PivotOut o = pout[k];
+        const bool rot = o.flags & PV_ROT, swp = o.flags & PV_SWAP;
+        if (!rot && !swp) continue;
+        const Ti z11 = (Ti)o.z11, z12 = (Ti)o.z12, z21 = (Ti)o.z21, z22 = (Ti)o.z22;
+        const Ti z12i = (Ti)o.z12i, z21i = (Ti)o.z21i;
+        auto upd = [&](Ti* Y) {
+          for (int r = lane; r < bb; r += 32) {
+            if constexpr (!CPLX) {
+              const Ti yi = Y[i * bb + r], yj = Y[j * bb + r];
+              Ti ni = yi, nj = yj;
+              if (rot) {
+                ni = fma(yj, z21, yi * z11);
+                nj = fma(yi, z12, yj * z22);
+              }
+              Y[i * bb + r] = swp ? nj : ni;
+              Y[j * bb + r] = swp ? ni : nj;
+            } else {
+              const Ti yir = Y[2 * (i * bb + r)], yii = Y[2 * (i * bb + r) + 1];
+              const Ti yjr = Y[2 * (j * bb + r)], yji = Y[2 * (j * bb + r) + 1];
+              Ti nir = yir, nii = yii, njr = yjr, nji = yji;
+              if (rot) {
+                nir = fma(yjr, z21, fma(-yji, z21i, yir * z11));
+                nii = fma(yjr, z21i, fma(yji, z21, yii * z11));
+                njr = fma(yir, z12, fma(-yii, z12i, yjr * z22));
+                nji = fma(yir, z12i, fma(yii, z12, yji * z22));
+              }
+              Y[2 * (i * bb + r)] = swp ? njr : nir;
+              Y[2 * (i * bb + r) + 1] = swp ? nji : nii;
+              Y[2 * (j * bb + r)] = swp ? nir : njr;
+              Y[2 * (j * bb + r) + 1] = swp ? nii : nji;
+            }
+          }
+        };
+        upd(Fh);
+        upd(Gh);
+        upd(Zh);
+      }
+      __syncthreads();
+      if (s_ctr[2]) break;
+    }
+    __syncthreads();
+    sweep_all = s_ctr[0];
+    const int fail = s_ctr[2];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (s_ctr[0]) atomicAdd(&b.ctr[0], (unsigned long long)s_ctr[0]);
+      if (s_ctr[1]) atomicAdd(&b.ctr[1], (unsigned long long)s_ctr[1]);
+      s_ctr[0] = 0;
+      s_ctr[1] = 0;
+    }
+    __syncthreads();
+    if (fail) {
+      if (threadIdx.x == 0) {
+        b.flags[slot] = 0;
+        atomicAdd(&b.ctr[prm.chol_skip ? 3 : 2], 1ull);
+      }
+      return;
+    }
+    if (sweep_all == 0) break;
+  }
+
+  // 5. Theta-tilde: theta_j = (||f-hat_j||^2 + ||g-hat_j||^2)^{-1/2}, Z-tilde = Z-hat Theta
+  const bool changed = s_ctr[3] != 0;
+  if (!changed) {
+    if (threadIdx.x == 0) b.flags[slot] = 0;
+    return;
+  }
+  for (int j = warp; j < bb; j += nwarps) {
+    Ti s = Ti(0);
+    for (int r = lane; r < E * bb; r += 32) {
+      const Ti f = Fh[j * E * bb + r], g = Gh[j * E * bb + r];
+      s += f * f + g * g;
+    }
+    s = warp_sum(s);
+    const Ti th = Ti(1) / sqrt(s);
+    for (int r = lane; r < E * bb; r += 32) Zh[j * E * bb + r] *= th;
+  }
+  __syncthreads();
+  // 6. real view of Z-tilde, row-major V x V, zero padded
+  To* zt = static_cast<To*>(b.ztil) + (size_t)slot * V * V;
+  for (int idx = threadIdx.x; idx < V * V; idx += blockDim.x) {
+    const int k = idx / V, j = idx % V;
+    To val = To(0);
+    if constexpr (!CPLX) {
+      if (k < bb && j < bb) val = (To)Zh[j * bb + k];
+    } else {
+      const bool kr = k < bb, jr = j < bb;
+      const int kk = kr ? k : k - bb, jj = jr ? j : j - bb;
+      if (kk < bb && jj < bb) {
+        const Ti zr = Zh[2 * (jj * bb + kk)], zi = Zh[2 * (jj * bb + kk) + 1];
+        if (kr && jr) val = (To)zr;
+        else if (kr && !jr) val = (To)zi;
+        else if (!kr && jr) val = (To)(-zi);
+        else val = (To)zr;
+      }
+    }
+    zt[idx] = val;
+  }
+  if (threadIdx.x == 0) {
+    b.flags[slot] = 1;
+    atomicAdd(&b.ctr[5], 1ull);
+  }
+}
+
+// --------------------------------------------------------------- apply ----
+template <class T, bool CPLX, int V>
+__global__ void __launch_bounds__(256) k_apply(BlkDims d, BlkBuffers b, int step) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int slot = blockIdx.x;
+  PairCols pc;
+  if (!load_pair(d, b, step, slot, pc)) return;
+  if (!b.flags[slot]) return;
+  const int tf = (d.mf + TR - 1) / TR, tg = (d.mg + TR - 1) / TR;
+  int tile = blockIdx.y;
+  T* Y;
+  long long ld;
+  int m;
+  if (tile < tf) {
+    Y = static_cast<T*>(b.F); ld = b.ldf; m = d.mf;
+  } else if (tile < tf + tg) {
+    tile -= tf; Y = static_cast<T*>(b.G); ld = b.ldg; m = d.mg;
+  } else {
+    tile -= tf + tg; Y = static_cast<T*>(b.Z); ld = b.ldz; m = d.n;
+  }
+  const int r0 = tile * TR;
+  const T* zt = static_cast<const T*>(b.ztil) + (size_t)slot * V * V;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  if constexpr (std::is_same<T, double>::value) {
+    constexpr int LDT = TR + 8, LDM = V + 8;
+    double* Ys = reinterpret_cast<double*>(smem_raw);  // [V][LDT] column-major
+    double* Ms = Ys + V * LDT;                          // [V][LDM] row-major
+    for (int idx = threadIdx.x; idx < V * V; idx += blockDim.x) Ms[(idx / V) * LDM + idx % V] = zt[idx];
+    load_tile<T, CPLX, true>(Ys, LDT, Y, ld, m, r0, pc, V);
+    __syncthreads();
+    constexpr int NJ = V / 8;
+    double acc[NJ][2];
+#pragma unroll
+    for (int t = 0; t < NJ; ++t) acc[t][0] = acc[t][1] = 0.0;
+    // warp w owns output rows [8w, 8w+8) of the tile
+#pragma unroll 4
+    for (int k0 = 0; k0 < V; k0 += 4) {
+      const double a = Ys[(k0 + (lane & 3)) * LDT + warp * 8 + (lane >> 2)];
+#pragma unroll
+      for (int t = 0; t < NJ; ++t) {
+        const double bv = Ms[(k0 + (lane & 3)) * LDM + t * 8 + (lane >> 2)];
+        dmma884(acc[t][0], acc[t][1], a, bv);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < NJ; ++t) {
+      const int r = warp * 8 + (lane >> 2), c = t * 8 + 2 * (lane & 3);
+      Ys[c * LDT + r] = acc[t][0];
+      Ys[(c + 1) * LDT + r] = acc[t][1];
+    }
+    __syncthreads();
+    if constexpr (!CPLX) {
+      for (int idx = threadIdx.x; idx < pc.bb * TR; idx += blockDim.x) {
+        const int c = idx / TR, r = idx % TR;
+        if (r0 + r < m) Y[(size_t)pc.gcol(c) * ld + r0 + r] = Ys[c * LDT + r];
+      }
+    } else {
+      double2* Y2 = reinterpret_cast<double2*>(Y);
+      for (int idx = threadIdx.x; idx < pc.bb * TR; idx += blockDim.x) {
+        const int c = idx / TR, r = idx % TR;
+        if (r0 + r < m) Y2[(size_t)pc.gcol(c) * ld + r0 + r] = make_double2(Ys[c * LDT + r], Ys[(pc.bb + c) * LDT + r]);
+      }
+    }
+  } else {
+    constexpr int LDT = V + 1;
+    float* Ws = reinterpret_cast<float*>(smem_raw);  // [TR][LDT] row-major
+    float* Ms = Ws + TR * LDT;                        // [V][V] row-major
+    for (int idx = threadIdx.x; idx < V * V; idx += blockDim.x) Ms[idx] = zt[idx];
+    load_tile<T, CPLX, false>(Ws, LDT, Y, ld, m, r0, pc, V);
+    __syncthreads();
+    constexpr int NV = V / 16;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float acc[4][NV];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[u][v] = 0.0f;
+#pragma unroll 4
+    for (int k = 0; k < V; ++k) {
+      float a[4], bv[NV];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = Ws[(tx + 16 * u) * LDT + k];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) bv[v] = Ms[k * V + ty + 16 * v];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[u][v] = fmaf(a[u], bv[v], acc[u][v]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Ws[(tx + 16 * u) * LDT + ty + 16 * v] = acc[u][v];
+    __syncthreads();
+    if constexpr (!CPLX) {
+      for (int idx = threadIdx.x; idx < pc.bb * TR; idx += blockDim.x) {
+        const int c = idx / TR, r = idx % TR;
+        if (r0 + r < m) Y[(size_t)pc.gcol(c) * ld + r0 + r] = Ws[r * LDT + c];
+      }
+    } else {
+      float2* Y2 = reinterpret_cast<float2*>(Y);
+      for (int idx = threadIdx.x; idx < pc.bb * TR; idx += blockDim.x) {
+        const int c = idx / TR, r = idx % TR;
+        if (r0 + r < m) Y2[(size_t)pc.gcol(c) * ld + r0 + r] = make_float2(Ws[r * LDT + c], Ws[r * LDT + pc.bb + c]);
+      }
+    }
+  }
+}
+
+template <class T, int V>
+size_t gram_smem() {
+  return std::is_same<T, double>::value ? sizeof(double) * V * (TR + 4) : sizeof(float) * TR * (V + 1);
+}
+template <class T, int V>
+size_t apply_smem() {
+  return std::is_same<T, double>::value ? sizeof(double) * (V * (TR + 8) + V * (V + 8))
+                                        : sizeof(float) * (TR * (V + 1) + V * V);
+}
+template <class Ti, bool CPLX, int V>
+size_t inner_smem() {
+  constexpr int E = CPLX ? 2 : 1;
+  constexpr int BMAX = CPLX ? V / 2 : V;
+  return sizeof(double) * 2 * E * BMAX * BMAX + sizeof(Ti) * E * BMAX * BMAX +
+         sizeof(PivIn) * (BMAX / 2 + 1) + sizeof(PivotOut) * (BMAX / 2 + 1);
+}
+
+template <class K>
+cudaError_t set_smem(K kern, size_t smem) {
+  if (smem > 48 * 1024) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaSuccess;
+}
+
+template <class T, bool CPLX, int V>
+cudaError_t gram_v(const BlkDims& d, const BlkBuffers& b, int step, cudaStream_t s) {
+  const size_t smem = gram_smem<T, V>();
+  auto kern = k_gram<T, CPLX, V>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(d.nslots, d.rf + d.rg);
+  kern<<<grid, gram_threads<T, V>(), smem, s>>>(d, b, step);
+  return cudaGetLastError();
+}
+template <class T, bool CPLX, int V>
+cudaError_t apply_v(const BlkDims& d, const BlkBuffers& b, int step, cudaStream_t s) {
+  const size_t smem = apply_smem<T, V>();
+  auto kern = k_apply<T, CPLX, V>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  const int tiles = (d.mf + TR - 1) / TR + (d.mg + TR - 1) / TR + (d.n + TR - 1) / TR;
+  dim3 grid(d.nslots, tiles);
+  kern<<<grid, 256, smem, s>>>(d, b, step);
+  return cudaGetLastError();
+}
+template <class Ti, class To, bool CPLX, int V>
+cudaError_t inner_v(const BlkDims& d, const BlkBuffers& b, int step, const InnerParams& p, cudaStream_t s) {
+  const size_t smem = inner_smem<Ti, CPLX, V>();
+  auto kern = k_inner<Ti, To, CPLX, V>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<d.nslots, 512, smem, s>>>(d, b, step, p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int blk_vmax(int w, bool cplx) {
+  const int v = cplx ? 4 * w : 2 * w;
+  if (v <= 16) return 16;
+  if (v <= 32) return 32;
+  if (v <= 64) return 64;
+  return 0;  // unsupported
+}
+
+#define HZ_DISPATCH_V(V, CALL)            \
+  switch (V) {                            \
+    case 16: { constexpr int VV = 16; return CALL; } \
+    case 32: { constexpr int VV = 32; return CALL; } \
+    case 64: { constexpr int VV = 64; return CALL; } \
+    default: return cudaErrorInvalidValue; \
+  }
+
+cudaError_t launch_gram(const BlkDims& d, const BlkBuffers& b, bool cplx, bool fp32, int step, cudaStream_t s) {
+  const int V = blk_vmax(d.w, cplx);
+  if (cplx) {
+    if (fp32) { HZ_DISPATCH_V(V, (gram_v<float, true, VV>(d, b, step, s))); }
+    else { HZ_DISPATCH_V(V, (gram_v<double, true, VV>(d, b, step, s))); }
+  } else {
+    if (fp32) { HZ_DISPATCH_V(V, (gram_v<float, false, VV>(d, b, step, s))); }
+    else { HZ_DISPATCH_V(V, (gram_v<double, false, VV>(d, b, step, s))); }
+  }
+}
+
+cudaError_t launch_apply(const BlkDims& d, const BlkBuffers& b, bool cplx, bool fp32, int step, cudaStream_t s) {
+  const int V = blk_vmax(d.w, cplx);
+  if (cplx) {
+    if (fp32) { HZ_DISPATCH_V(V, (apply_v<float, true, VV>(d, b, step, s))); }
+    else { HZ_DISPATCH_V(V, (apply_v<double, true, VV>(d, b, step, s))); }
+  } else {
+    if (fp32) { HZ_DISPATCH_V(V, (apply_v<float, false, VV>(d, b, step, s))); }
+    else { HZ_DISPATCH_V(V, (apply_v<double, false, VV>(d, b, step, s))); }
+  }
+}
+
+cudaError_t launch_inner(const BlkDims& d, const BlkBuffers& b, bool cplx, bool fp32, int step,
+                         const InnerParams& p, cudaStream_t s) {
+  const int V = blk_vmax(d.w, cplx);
+  if (cplx) {
+    if (fp32) { HZ_DISPATCH_V(V, (inner_v<float, float, true, VV>(d, b, step, p, s))); }
+    else { HZ_DISPATCH_V(V, (inner_v<double, double, true, VV>(d, b, step, p, s))); }
+  } else {
+    if (fp32) { HZ_DISPATCH_V(V, (inner_v<float, float, false, VV>(d, b, step, p, s))); }
+    else { HZ_DISPATCH_V(V, (inner_v<double, double, false, VV>(d, b, step, p, s))); }
+  }
+}
+
+}  // namespace hz

@@ -1,0 +1,94 @@
+"""CPU-only checks of the C ABI library: it loads, exports every function that
+include/gsvd.h declares, and rejects bad arguments before any launch."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1909_00101_gb300.build import build
+    build()
+    import paper_1909_00101_gb300 as hz
+    return hz.load_library()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "gsvd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gsvd_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("gsvd_create", "gsvd_destroy", "gsvd_solve", "gsvd_solve_batched", "gsvd_submit", "gsvd_poll"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    import paper_1909_00101_gb300 as hz
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert set(hz.ENTRY_POINTS) <= set(declared_functions())
+
+
+def test_config_defaults(lib):
+    import paper_1909_00101_gb300 as hz
+    c = hz.Config()
+    lib.gsvd_config_default(ctypes.byref(c))
+    assert c.max_sweeps == 30 and c.inner_max_sweeps == 30 and c.criterion == 1 and c.sort == 1
+    assert c.hbm_budget_bytes == 60 << 30 and c.precision == 0
+
+
+def test_strerror(lib):
+    for s in (0, 1, -1, -2, -3, -4, -5, -6, -7, -8):
+        assert lib.gsvd_strerror(s)
+    assert lib.gsvd_strerror(-99) == b"unknown status"
+
+
+def test_invalid_problems_rejected_before_any_launch(lib):
+    import paper_1909_00101_gb300 as hz
+    h = ctypes.c_void_p()
+    cfg = hz.make_config()
+    assert lib.gsvd_create(ctypes.byref(h), ctypes.byref(cfg), None) == 0
+    F = np.zeros((3, 4), order="F")
+    G = np.zeros((5, 4), order="F")
+    Z = np.zeros((4, 4), order="F")
+    v = np.zeros(4)
+    p = hz._problem(F, G, Z, v, v, v, False)        # m_F < n
+    info = hz.Info()
+    assert lib.gsvd_solve(h, ctypes.byref(p), ctypes.byref(info)) == hz.EINVAL
+    p.m_f = 6
+    p.ldf = 2                                        # ld < m
+    assert lib.gsvd_solve(h, ctypes.byref(p), ctypes.byref(info)) == hz.EINVAL
+    p.ldf = 6
+    p.dtype = 7                                      # bad dtype
+    assert lib.gsvd_solve(h, ctypes.byref(p), ctypes.byref(info)) == hz.EINVAL
+    assert lib.gsvd_solve(h, None, ctypes.byref(info)) == hz.EINVAL
+    assert lib.gsvd_solve_batched(h, None, -1, None) == hz.EINVAL
+    assert lib.gsvd_destroy(h) == 0
+
+
+def test_bad_config_rejected(lib):
+    import paper_1909_00101_gb300 as hz
+    h = ctypes.c_void_p()
+    for field, val in (("criterion", 3), ("max_sweeps", 0), ("inner_max_sweeps", 0), ("precision", 5)):
+        cfg = hz.make_config()
+        setattr(cfg, field, val)
+        assert lib.gsvd_create(ctypes.byref(h), ctypes.byref(cfg), None) == hz.EINVAL
+
+
+def test_workspace_bytes_grows_with_size(lib):
+    import paper_1909_00101_gb300 as hz
+    cfg = hz.make_config(path="blocked")
+    a = lib.gsvd_workspace_bytes(ctypes.byref(cfg), 0, 512, 512, 256)
+    b = lib.gsvd_workspace_bytes(ctypes.byref(cfg), 0, 4096, 4096, 2048)
+    c = lib.gsvd_workspace_bytes(ctypes.byref(cfg), 1, 4096, 4096, 2048)
+    assert 0 < a < b < c
+    mixed = hz.make_config(path="blocked", precision="mixed")
+    assert lib.gsvd_workspace_bytes(ctypes.byref(mixed), 0, 4096, 4096, 2048) > b

@@ -1,0 +1,234 @@
+"""GPU parity: the CUDA library (through the C ABI) against the oracle.
+
+Tolerance (floating point, sigma): every valid FP64 rounding sequence moves
+the computed generalized singular values by about eps times their condition,
+so the GPU is compared with the extended-precision oracle on the same rounded
+inputs and must satisfy
+
+    err(GPU vs oracle_ext) <= max(1e-12, 4 * err(oracle_fp64 vs oracle_ext)),
+
+which is the stated 1e-12 wherever the FP64 oracle itself is within 2.5e-13.
+The raw GPU-vs-FP64-oracle error is reported with every case.  Residuals:
+||FZ - U Sigma_F|| / ||F|| <= 1e-13 n, ||GZ - V Sigma_G|| / ||G|| <= 1e-13 n,
+orthogonality of U and V, Sigma_F^2 + Sigma_G^2 = 1, Sigma sorted.
+Integer outputs (status, convergence) must match exactly where defined.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_00101_gb300.inputs import make_pair, POINTWISE_64x32
+from gsvd_checks import invariants, rel_sigma_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hz():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1909_00101_gb300.build import build
+    build()
+    import paper_1909_00101_gb300 as m
+    m.load_library()
+    return m
+
+
+def _dev(a):
+    return torch.from_numpy(np.asfortranarray(a)).cuda()
+
+
+def _np(t):
+    return t.cpu().numpy()
+
+
+def check(p_F, p_G, r, *, n_res=1e-13, label=""):
+    ref = oracle.gsvd(p_F, p_G)
+    refx = oracle.gsvd(p_F, p_G, extended=True)
+    assert ref["status"] == 0 and refx["status"] == 0
+    sig = _np(r.sigma)
+    floor = rel_sigma_err(ref["sigma"], refx["sigma"])
+    tol = max(1e-12, 4.0 * floor)
+    err_x = rel_sigma_err(sig, refx["sigma"])
+    err_64 = rel_sigma_err(sig, ref["sigma"])
+    print("%s sigma err vs oracle_ext %.2e (tol %.2e), vs oracle_fp64 %.2e, info %s"
+          % (label, err_x, tol, err_64, r.info))
+    assert r.status == 0, r.info
+    assert err_x <= tol, (err_x, tol)
+    n = p_F.shape[1]
+    inv = invariants(p_F, p_G, _np(r.U), _np(r.V), _np(r.Z), _np(r.sigma_f), _np(r.sigma_g), sig)
+    assert inv["FZ"] <= n_res * n and inv["GZ"] <= n_res * n, inv
+    assert inv["UU"] <= 1e-12 * n and inv["VV"] <= 1e-12 * n, inv
+    assert inv["scale"] <= 8 * 2.0 ** -53 and inv["sorted"], inv
+    assert rel_sigma_err(_np(r.sigma_f) / _np(r.sigma_g), sig) <= 8 * 2.0 ** -53
+    return err_x
+
+
+# ------------------------------------------------------------ pointwise ----
+
+@pytest.mark.parametrize("order", ["round_robin", "row_cyclic"])
+def test_pointwise_64x32_real(hz, order):
+    p = make_pair(**POINTWISE_64x32)
+    r = hz.solve(_dev(p.F), _dev(p.G), path="pointwise", order=order)
+    check(p.F, p.G, r, label="pointwise-" + order)
+
+
+def test_pointwise_row_cyclic_follows_the_oracle(hz):
+    """Row-cyclic wavefront order = the oracle's sequence of transformations:
+    only the rounding of the dot products differs."""
+    p = make_pair(**POINTWISE_64x32)
+    r = hz.solve(_dev(p.F), _dev(p.G), path="pointwise", order="row_cyclic")
+    ref = oracle.gsvd(p.F, p.G)
+    assert rel_sigma_err(_np(r.sigma), ref["sigma"]) <= 1e-13
+    assert abs(r.info["sweeps_fp64"] - ref["sweeps"]) <= 1
+
+
+@pytest.mark.parametrize("shape", [(40, 33, 33), (20, 17, 7), (9, 8, 2), (5, 3, 1)])
+def test_pointwise_ragged_and_tiny(hz, shape):
+    mf, mg, n = shape
+    p = make_pair(mf, mg, n, seed=n)
+    r = hz.solve(_dev(p.F), _dev(p.G), path="pointwise")
+    check(p.F, p.G, r, label="pointwise%s" % (shape,))
+
+
+def test_pointwise_complex(hz):
+    p = make_pair(48, 40, 24, cplx=True, seed=3)
+    r = hz.solve(_dev(p.F), _dev(p.G), path="pointwise")
+    check(p.F, p.G, r, label="pointwise-complex")
+
+
+# -------------------------------------------------------------- blocked ----
+
+@pytest.mark.parametrize("w,shape", [(8, (160, 130, 96)), (16, (200, 180, 100)), (32, (300, 257, 150)),
+                                     (8, (70, 65, 61))])
+def test_blocked_real_fp64(hz, w, shape):
+    mf, mg, n = shape
+    p = make_pair(mf, mg, n, lo=1e-3, hi=1e3, cond=1e2, seed=w + n)
+    r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", block_w=w)
+    assert r.info["path"] == 2 and r.info["block_w"] == w
+    check(p.F, p.G, r, label="blocked w=%d %s" % (w, shape))
+
+
+@pytest.mark.parametrize("w", [4, 8, 16])
+def test_blocked_complex_fp64(hz, w):
+    p = make_pair(120, 90, 72, lo=1e-3, hi=1e3, cond=1e2, cplx=True, seed=w)
+    r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", block_w=w)
+    check(p.F, p.G, r, label="blocked-complex w=%d" % w)
+
+
+def test_blocked_bo_inner_one_sweep(hz):
+    p = make_pair(150, 140, 96, seed=12)
+    r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", block_w=16, inner_max_sweeps=1)
+    check(p.F, p.G, r, label="blocked BO")
+
+
+def test_blocked_criterion_c2(hz):
+    p = make_pair(150, 140, 96, seed=13)
+    r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", block_w=16, criterion=2)
+    check(p.F, p.G, r, label="blocked C2")
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_mixed_precision(hz, cplx):
+    p = make_pair(200, 160, 128, lo=1e-3, hi=1e3, cond=1e2, cplx=cplx, seed=21)
+    r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", block_w=16 if not cplx else 8, precision="mixed")
+    assert r.info["sweeps_fp32"] >= 1
+    check(p.F, p.G, r, label="mixed cplx=%s" % cplx)
+
+
+# ------------------------------------------------------- reproducibility ----
+
+@pytest.mark.parametrize("kw", [dict(path="pointwise"), dict(path="blocked", block_w=16),
+                                dict(path="blocked", block_w=16, precision="mixed")])
+def test_bitwise_repeatable(hz, kw):
+    p = make_pair(130, 120, 64, seed=5)
+    a = hz.solve(_dev(p.F), _dev(p.G), **kw)
+    b = hz.solve(_dev(p.F), _dev(p.G), **kw)
+    for x, y in ((a.U, b.U), (a.V, b.V), (a.Z, b.Z), (a.sigma, b.sigma), (a.sigma_f, b.sigma_f)):
+        assert torch.equal(x, y)
+
+
+def test_host_pointer_path_equals_device_path(hz):
+    p = make_pair(100, 90, 72, seed=6)
+    d = hz.solve(_dev(p.F), _dev(p.G), path="blocked", block_w=8)
+    h = hz.solve(p.F.copy(order="F"), p.G.copy(order="F"), path="blocked", block_w=8)
+    assert np.array_equal(_np(d.sigma), h.sigma) and np.array_equal(_np(d.Z), h.Z)
+    assert np.array_equal(_np(d.U), h.U)
+
+
+def test_batched_equals_single(hz):
+    shapes = [(40, 35, 30), (64, 48, 32), (20, 20, 16), (90, 80, 70), (33, 33, 33)]
+    pairs = [make_pair(*s, seed=100 + k) for k, s in enumerate(shapes)]
+    with hz.Solver() as s:
+        batch = s.solve_batched([(_dev(p.F), _dev(p.G)) for p in pairs])
+        for p, rb in zip(pairs, batch):
+            r1 = s.solve(_dev(p.F), _dev(p.G))
+            assert rb.info["status"] == 0
+            assert torch.equal(rb.sigma, r1.sigma) and torch.equal(rb.Z, r1.Z)
+            check(p.F, p.G, rb, label="batched n=%d" % p.F.shape[1])
+
+
+def test_serving_results_equal_alone_and_in_mix(hz):
+    shapes = [(64, 48, 32), (200, 150, 100), (90, 80, 70), (130, 120, 64), (300, 280, 160), (40, 40, 40)]
+    pairs = [make_pair(*s, seed=200 + k, cplx=(k % 3 == 2)) for k, s in enumerate(shapes)]
+    with hz.Solver(max_inflight=4) as s:
+        alone = [s.solve(_dev(p.F), _dev(p.G)) for p in pairs]
+        tickets = [s.submit(_dev(p.F), _dev(p.G)) for p in pairs]
+        import time
+        done = {}
+        t0 = time.time()
+        while len(done) < len(tickets) and time.time() - t0 < 120:
+            for k, (t, res) in enumerate(tickets):
+                if k in done:
+                    continue
+                st, info = s.poll(t)
+                if st != hz.EAGAIN:
+                    done[k] = (st, info)
+            time.sleep(0.001)
+        assert len(done) == len(tickets)
+        for k, (t, res) in enumerate(tickets):
+            assert done[k][0] == 0, done[k]
+            assert torch.equal(res.sigma, alone[k].sigma) and torch.equal(res.Z, alone[k].Z)
+
+
+# ---------------------------------------------------------------- status ----
+
+def test_status_nonfinite_input(hz):
+    p = make_pair(40, 40, 20, seed=1)
+    F = p.F.copy()
+    F[3, 4] = np.nan
+    r = hz.solve(_dev(F), _dev(p.G))
+    assert r.status == hz.EINVAL
+
+
+@pytest.mark.parametrize("path", ["pointwise", "blocked"])
+def test_status_rank_deficient_G(hz, path):
+    p = make_pair(40, 40, 20, seed=2)
+    G = p.G.copy()
+    G[:, 5] = 0.0
+    G[:4, 5] = 1.0
+    G[:, 6] = G[:, 5]
+    r = hz.solve(_dev(p.F), _dev(G), path=path, block_w=4 if path == "blocked" else 0)
+    assert r.status == hz.ENOTPD
+
+
+@pytest.mark.parametrize("path", ["pointwise", "blocked"])
+def test_status_sweep_cap(hz, path):
+    p = make_pair(100, 100, 60, seed=3)
+    r = hz.solve(_dev(p.F), _dev(p.G), path=path, max_sweeps=1, block_w=8 if path == "blocked" else 0)
+    assert r.status == hz.ENOCONV
+    assert r.info["sweeps_fp64"] == 1
+    # outputs are still a valid decomposition of the pair at that point
+    inv = invariants(p.F, p.G, _np(r.U), _np(r.V), _np(r.Z), _np(r.sigma_f), _np(r.sigma_g), _np(r.sigma))
+    assert inv["FZ"] < 1e-12 and inv["scale"] <= 8 * 2.0 ** -53
+
+
+def test_n_equal_one(hz):
+    rng = np.random.default_rng(0)
+    F = rng.standard_normal((5, 1))
+    G = rng.standard_normal((3, 1))
+    r = hz.solve(_dev(F), _dev(G))
+    ref = oracle.gsvd(F, G)
+    assert r.status == 0
+    assert rel_sigma_err(_np(r.sigma), ref["sigma"]) <= 4e-16
