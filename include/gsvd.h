@@ -156,6 +156,33 @@ uint64_t gsvd_workspace_bytes(const gsvd_config *cfg, int32_t dtype, int64_t m_f
 /* Static text of a status code. */
 const char *gsvd_strerror(int status);
 
+/* ---- allocation-free batch of small problems --------------------------------
+ * The paper has no counterpart of this entry point; it exists for callers that
+ * must not allocate device memory: code whose device memory is owned by its own
+ * pool allocator, latency-critical loops in which cudaMalloc/cudaFree would
+ * synchronize the device, host callbacks that may not enter the allocator.
+ *
+ * Solves count independent problems on the pointwise kernel (one CTA per
+ * problem) exactly as gsvd_solve_batched does for small problems, but without
+ * any device or pinned allocation: the kernel's scratch (the descriptor table
+ * it reads and the status records it writes) is a fixed array of about 480 KiB
+ * compiled into the library, which every GPU that loads the library keeps until
+ * the process exits.  Limits: count <= GSVD_NOALLOC_MAX_PROBLEMS and n <= 64
+ * with F, G, Z fitting in shared memory (else GSVD_ETOOBIG); every pointer of
+ * every problem must be device memory (else GSVD_EINVAL).  cfg may be NULL
+ * (defaults; precision, path and block width are ignored: FP64 pointwise).
+ * cuda_stream: a cudaStream_t of the current device, NULL = legacy stream.
+ *
+ * The first call on a device (with that device current) looks up the array's
+ * device address; make that first call before any stream capture.  Every call
+ * reuses the same array, so calls are serialized inside the library: two
+ * calls on the same device whose work overlapped on the GPU would race on it.
+ * Returns GSVD_OK if every problem succeeded, else the first failing status;
+ * infos (may be NULL) receives one report per problem. */
+#define GSVD_NOALLOC_MAX_PROBLEMS 4096
+int gsvd_solve_small_noalloc(const gsvd_problem *ps, int32_t count, const gsvd_config *cfg,
+                             void *cuda_stream, gsvd_info *infos);
+
 #ifdef __cplusplus
 }
 #endif

@@ -64,7 +64,8 @@ class Info(ctypes.Structure):
 
 
 ENTRY_POINTS = ("gsvd_config_default", "gsvd_create", "gsvd_destroy", "gsvd_solve", "gsvd_solve_batched",
-                "gsvd_submit", "gsvd_poll", "gsvd_workspace_bytes", "gsvd_strerror")
+                "gsvd_submit", "gsvd_poll", "gsvd_workspace_bytes", "gsvd_strerror", "gsvd_solve_small_noalloc")
+NOALLOC_MAX_PROBLEMS = 4096
 
 _lib = None
 
@@ -90,6 +91,8 @@ def load_library(path: str = LIB_PATH):
     lib.gsvd_workspace_bytes.restype = ctypes.c_uint64
     lib.gsvd_strerror.argtypes = [ctypes.c_int]
     lib.gsvd_strerror.restype = ctypes.c_char_p
+    lib.gsvd_solve_small_noalloc.argtypes = [P(Problem), ctypes.c_int32, P(Config), ctypes.c_void_p, P(Info)]
+    lib.gsvd_solve_small_noalloc.restype = ctypes.c_int
     for name in ("gsvd_create", "gsvd_destroy", "gsvd_solve", "gsvd_solve_batched", "gsvd_submit", "gsvd_poll"):
         getattr(lib, name).restype = ctypes.c_int
     if path == LIB_PATH:
@@ -286,6 +289,31 @@ class Solver:
 
     def workspace_bytes(self, dtype: int, mf: int, mg: int, n: int) -> int:
         return int(self._lib.gsvd_workspace_bytes(ctypes.byref(self.config), dtype, mf, mg, n))
+
+
+def solve_small_noalloc(pairs, *, stream=None, **cfg) -> tuple:
+    """Batch of small device problems (n <= 64) through gsvd_solve_small_noalloc.
+
+    The library allocates no device memory for this call: the kernel's scratch
+    is a fixed array inside the library.  For callers that must not allocate
+    (a framework owning all device memory, a loop where cudaMalloc would
+    synchronize).  The output buffers here are allocated by torch on the
+    Python side, before the call.  Returns (status, [Result, ...]).
+    """
+    import torch
+    lib = load_library()
+    preps = [_prepare(F, G, False) for F, G in pairs]
+    probs = [_problem(Fc, Gc, Z, sf, sg, sig, True) for (_, Fc, Gc, Z, sf, sg, sig) in preps]
+    arr = (Problem * len(probs))(*probs)
+    infos = (Info * len(probs))()
+    c = make_config(**cfg)
+    s = 0
+    if stream is not None:
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    torch.cuda.current_stream().synchronize()
+    st = lib.gsvd_solve_small_noalloc(arr, len(probs), ctypes.byref(c), ctypes.c_void_p(s), infos)
+    res = [Result(Fc, Gc, Z, sf, sg, sig, inf.as_dict()) for (_, Fc, Gc, Z, sf, sg, sig), inf in zip(preps, infos)]
+    return st, res
 
 
 def solve(F, G, *, inplace: bool = False, **cfg) -> Result:
