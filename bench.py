@@ -173,10 +173,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--block-w", type=int, default=0)
-    ap.add_argument("--inner", type=int, default=0, help="inner sweep cap (0 = library default)")
+    ap.add_argument("--inner", type=int, default=1, help="inner sweep cap of the FP64 sweeps (1 = BO, 30 = FB)")
+    ap.add_argument("--max-sweeps", type=int, default=60)
     ap.add_argument("--compare", type=int, default=1, help="also time the other precision (1 step)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-baseline", type=int, default=1)
+    ap.add_argument("--clocks", type=int, default=1, help="0: no nvidia-smi sampling (profiler runs)")
     args = ap.parse_args()
 
     if args.impl == "reference":
@@ -209,7 +211,8 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     def make_solver(prec, profile):
-        kw = dict(precision=prec, path="blocked", profile=profile)
+        kw = dict(precision=prec, path="blocked", profile=profile, max_sweeps=args.max_sweeps,
+                  fp32_max_sweeps=args.max_sweeps)
         if args.block_w:
             kw["block_w"] = args.block_w
         if args.inner:
@@ -234,7 +237,8 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     clocks = Clocks(local)
-    clocks.start()
+    if args.clocks:
+        clocks.start()
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     infos = []
     evs[0].record(stream)
@@ -263,7 +267,11 @@ def main():
     res_g = float(torch.linalg.norm(G0 @ Z - G * sg[None, :]) / torch.linalg.norm(G0))
     orth_u = float(torch.linalg.norm(F.t() @ F - torch.eye(n, dtype=torch.float64, device=dev)))
 
-    # roofline of the dominant kernel class (event-timed launches of the timed steps)
+    # roofline of every kernel class from the event-timed launches of the timed
+    # steps; the top-level entry is the dominant class.  Algorithmic work per
+    # pair visit (pair width b, m = m_F + m_G): Gram b(b+1) m flops, apply
+    # 2 b^2 (m + n) flops per applied visit, inner 2 b^3 / 3 (two Choleskys) +
+    # b(b-1)/2 pivots x 32 b flops (four dots of b, six column updates of b).
     names = ["gram_f64", "inner_f64", "apply_f64", "gram_f32", "inner_f32", "apply_f32"]
     tk = np.sum([i["t_kernel_us"] for i in infos], axis=0)
     nk = np.sum([i["n_kernel"] for i in infos], axis=0)
@@ -274,35 +282,37 @@ def main():
     applied = sum(i["visits_applied"] for i in infos)
     bf16, peak_note = measured_peaks()
     fp64_peak = bf16 * FP64_NOMINAL_TF / BF16_NOMINAL_TF
-    roof = None
-    if nk[dom] > 0:
-        avg_s = tk[dom] / nk[dom] / 1e6
-        nl = nk[dom]
-        if names[dom].startswith("gram"):
-            units = visits / max(1, (nk[0] + nk[3]))
+    rooflines = {}
+    for k in range(6):
+        if nk[k] == 0:
+            continue
+        avg_s = tk[k] / nk[k] / 1e6
+        fp32 = names[k].endswith("f32")
+        if names[k].startswith("gram"):
+            units = visits / max(1, nk[0] + nk[3])
             flops = units * b * (b + 1) * (mf + mg)
-        elif names[dom].startswith("apply"):
-            units = applied / max(1, (nk[2] + nk[5]))
+        elif names[k].startswith("apply"):
+            units = applied / max(1, nk[2] + nk[5])
             flops = units * 2.0 * b * b * (mf + mg + n)
         else:
-            units, flops = visits / max(1, nk[1] + nk[4]), None
-        fp32 = names[dom].endswith("f32")
-        if flops is not None:
-            ach = flops / avg_s / 1e12
-            if fp32:
-                roof = {"bound": "alu", "achieved": ach, "peak": FP32_ALU_PEAK_TF, "unit": "TFLOP/s",
-                        "frac": ach / FP32_ALU_PEAK_TF, "traffic": None, "kernel": names[dom],
-                        "peak_note": "FP32 FFMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"}
-            else:
-                roof = {"bound": "tensor", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                        "frac": ach / fp64_peak, "traffic": None, "kernel": names[dom],
-                        "peak_note": "FP64 DMMA: bf16 dense %s x 1.25/2250 nominal FP64/bf16" % peak_note}
+            units = visits / max(1, nk[1] + nk[4])
+            flops = units * (2.0 * b ** 3 / 3 + b * (b - 1) / 2 * 32.0 * b)
+        ach = flops / avg_s / 1e12
+        if fp32:
+            ent = {"bound": "alu", "achieved": ach, "peak": FP32_ALU_PEAK_TF, "unit": "TFLOP/s",
+                   "frac": ach / FP32_ALU_PEAK_TF, "traffic": None,
+                   "peak_note": "FP32 FFMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"}
         else:
-            roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
-                    "traffic": None, "kernel": names[dom], "note": "FP64-latency-bound inner level"}
-        roof["avg_launch_us"] = avg_s * 1e6
-        roof["launches"] = int(nl)
-        roof["units_per_launch"] = units
+            ent = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                   "frac": ach / fp64_peak, "traffic": None,
+                   "peak_note": "FP64 pipe (DMMA issues on it): bf16 dense %s x 1.25/2250 nominal FP64/bf16"
+                                % peak_note}
+        if names[k].startswith("inner"):
+            ent["note"] = "latency-bound: FP64 2x2 parameter chain per inner step, one CTA per pair visit"
+        ent.update({"kernel": names[k], "avg_launch_us": avg_s * 1e6, "launches": int(nk[k]),
+                    "units_per_launch": units, "flops_per_launch": flops})
+        rooflines[names[k]] = ent
+    roof = dict(rooflines[names[dom]]) if nk[dom] else None
     kshare = {names[k]: round(float(tk[k] / max(1e-9, tk.sum())), 4) for k in range(6) if nk[k]}
 
     out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -320,7 +330,7 @@ def main():
                                           "t_total_us", "t_fp32_us", "t_refine_us", "visits",
                                           "visits_applied", "chol_skipped")},
            "kernel_time_share": kshare,
-           "roofline": roof, "clocks": clk,
+           "roofline": roof, "rooflines": rooflines, "clocks": clk,
            "gpu_launches": None}
     # launches of our kernels in the timed region: per sweep 3 per outer step
     # plus prescale/rescale/finalize/check kernels

@@ -26,7 +26,7 @@ namespace {
 
 constexpr double EPS64 = 1.1102230246251565e-16;  // 2^-53
 constexpr double EPS32 = 5.9604644775390625e-08;  // 2^-24
-constexpr int POINTWISE_MAX_N = 64;
+constexpr int POINTWISE_MAX_N = 64;  // at most 32 pairs per step: one lane each
 constexpr int NCTR = 8;
 constexpr size_t SMEM_LIMIT = 227 * 1024;
 
@@ -157,11 +157,18 @@ bool make_plan(const gsvd_config& cfg, int dtype, int64_t mf, int64_t mg, int64_
   P.neff = P.nblk + (P.nblk & 1);
   P.nslots = P.neff / 2;
   P.steps = P.neff - 1;
-  // row splits: about four Gram CTAs per SM in total, at least 64 rows each
-  const int target = 4 * 152;
-  int s = std::max(2, (target + P.nslots - 1) / P.nslots);
-  P.rf = std::max(1, std::min((int)((mf + 63) / 64), (int)std::lround((double)s * mf / (double)(mf + mg))));
-  P.rg = std::max(1, std::min((int)((mg + 63) / 64), s - P.rf));
+  // row splits of the Gram: about twelve CTAs per SM in total (so the uneven
+  // last wave costs little), whole 64-row tiles per split, no empty split
+  {
+    const int target = 12 * 152;
+    const int s = std::max(2, (target + P.nslots - 1) / P.nslots);
+    const int tf = (int)((mf + 63) / 64), tg = (int)((mg + 63) / 64);
+    const int sf = std::max(1, (int)std::lround((double)s * tf / (double)(tf + tg)));
+    const int sg = std::max(1, s - sf);
+    const int pf = (tf + sf - 1) / sf, pg = (tg + sg - 1) / sg;  // tiles per split
+    P.rf = (tf + pf - 1) / pf;
+    P.rg = (tg + pg - 1) / pg;
+  }
   const size_t V2 = (size_t)P.V * P.V;
   size_t o = 0;
   P.off_partial = o; o = align256(o + (size_t)P.nslots * (P.rf + P.rg) * V2 * 8);

@@ -91,78 +91,106 @@ struct PivotOut {
 };
 enum : int { PV_ROT = 1, PV_BIG = 2, PV_SWAP = 4, PV_FAIL = 8 };
 
-// Real pivot, Sec. 2.1.2.  a11 = a_ii, a22 = a_jj, a12 = a_ij, x = b_ij;
-// tol = eps * sqrt(columns at this level); f32cls: classify small/big after
-// rounding the diagonal of Z-hat to FP32 (bulk FP32 sweeps); crit2: C2.
-__device__ __forceinline__ PivotOut pivot_real(double a11, double a22, double a12,
-                                               double x, double tol, bool sort,
-                                               bool f32cls, bool crit2) {
-  PivotOut o;
-  o.z12i = o.z21i = 0.0;
-  o.flags = 0;
+// Real pivot, Sec. 2.1.2, in two independent FP64 chains that can run on two
+// warps (two SM sub-partitions) at once -- on sm_103a a lone warp issues one
+// FP64 instruction per ~76 cycles, so the chain length sets the step latency:
+//   chain A: skip test, t = sqrt(1 - x^2) (with 1/t), cot 2theta as num/den,
+//            tan theta, cos theta, sin theta;
+//   chain B: xi = x / (sqrt(1+x) + sqrt(1-x)) and
+//            eta = x / ((1 + sqrt(1+x)) (1 + sqrt(1-x)));
+//   combine: cos/sin of phi and psi, Z-hat, sorting and the small/big class.
+// The chain below is the paper's, rearranged to need 7 instead of 11 square
+// roots and divisions: 1/t and t from one rsqrt; xi and eta from one
+// reciprocal; tan theta = sign(1, cot 2theta) / (|cot 2theta| +
+// sqrt(1 + cot^2 2theta)) written on num/den without forming the cotangent:
+// sign(num) den / (|num| + hypot(num, den)).
+enum : int { RC_SKIP = 0, RC_ROT = 1, RC_EXC = 2, RC_FAIL = 3 };
+struct RealChainA {
+  double rt, c, s;
+  int mode;
+};
+
+__device__ __forceinline__ RealChainA real_chain_a(double a11, double a22, double a12, double x, double tol) {
+  RealChainA r;
+  r.rt = 1.0; r.c = 1.0; r.s = 0.0;
   // relative orthogonality (Sec. 2.1), |a12| < sqrt(a11) sqrt(a22) tol and
   // |x| < tol, compared in squares (no FP64 square roots)
   const double tol2 = tol * tol;
   if (a12 * a12 < (a11 * a22) * tol2 && x * x < tol2) {
-    o.z11 = 1.0; o.z12 = 0.0; o.z21 = 0.0; o.z22 = 1.0;
-    if (sort && a11 < a22) o.flags |= PV_SWAP;
-    return o;
+    r.mode = RC_SKIP;
+    return r;
   }
   const double t2 = fma(-x, x, 1.0);
   if (!(t2 > 0.0)) {
-    o.z11 = 1.0; o.z12 = 0.0; o.z21 = 0.0; o.z22 = 1.0;
+    r.mode = RC_FAIL;
+    return r;
+  }
+  r.rt = rsqrt(t2);
+  const double t = t2 * r.rt;
+  const double num = t * (a22 - a11);
+  const double den = 2.0 * a12 - (a11 + a22) * x;
+  if (num == 0.0 && den == 0.0) {
+    r.mode = RC_EXC;  // proportional pivots: cot 2theta = 0/0
+    return r;
+  }
+  const double hyp = sqrt(fma(num, num, den * den));
+  const double tn = sgn1(num) * den / (fabs(num) + hyp);
+  r.c = rsqrt(fma(tn, tn, 1.0));
+  r.s = tn * r.c;
+  r.mode = RC_ROT;
+  return r;
+}
+
+__device__ __forceinline__ void real_chain_b(double x, double& xi, double& eta) {
+  const double sp = sqrt(1.0 + x), sm = sqrt(1.0 - x);
+  const double q1 = sp + sm, q2 = (1.0 + sp) * (1.0 + sm);
+  const double rq = 1.0 / (q1 * q2);
+  xi = x * q2 * rq;
+  eta = x * q1 * rq;
+}
+
+__device__ __forceinline__ PivotOut real_combine(double a11, double a22, double a12, double x,
+                                                 const RealChainA& r, double xi, double eta, bool sort,
+                                                 bool f32cls, bool crit2) {
+  PivotOut o;
+  o.z12i = o.z21i = 0.0;
+  o.flags = 0;
+  o.z11 = 1.0; o.z12 = 0.0; o.z21 = 0.0; o.z22 = 1.0;
+  if (r.mode == RC_SKIP) {
+    if (sort && a11 < a22) o.flags |= PV_SWAP;
+    return o;
+  }
+  if (r.mode == RC_FAIL) {
     o.flags = PV_FAIL;
     return o;
   }
-  // The chain below is the paper's (t, xi, eta, cot 2theta, tan theta, cos,
-  // sin, then cos/sin of phi and psi), rearranged to need 7 instead of 11
-  // square roots and divisions (each costs a few dozen FP64 instructions on
-  // sm_103a): 1/t and t from one rsqrt; xi and eta from one reciprocal; and
-  // tan theta = sign(1, cot 2theta) / (|cot 2theta| + sqrt(1 + cot^2 2theta))
-  // written on num/den without forming cot: sign(num) den / (|num| + hypot).
-  const double rt = rsqrt(t2);
-  const double t = t2 * rt;
-  const double num = t * (a22 - a11);
-  const double den = 2.0 * a12 - (a11 + a22) * x;
   double cphi, cpsi;
-  if (num == 0.0 && den == 0.0) {
-    // proportional pivots: signed form of the exception
+  if (r.mode == RC_EXC) {
+    // signed form of the exception (reading of Sec. 2.1.2)
     const double s = sgn1(x), ax = fabs(x);
     const double p = rsqrt(2.0 * (1.0 + ax)), q = rsqrt(2.0 * (1.0 - ax));
     o.z11 = p; o.z12 = -s * q; o.z21 = s * p; o.z22 = q;
     cphi = o.z11; cpsi = o.z22;  // no t in this form
-    o.flags = PV_ROT;
-    const bool small = f32cls ? (__double2float_rn(o.z11) == 1.0f && __double2float_rn(o.z22) == 1.0f)
-                              : (o.z11 == 1.0 && o.z22 == 1.0);
-    if (!small) o.flags |= PV_BIG;
   } else {
-    const double sp = sqrt(1.0 + x), sm = sqrt(1.0 - x);
-    const double q1 = sp + sm, q2 = (1.0 + sp) * (1.0 + sm);
-    const double rq = 1.0 / (q1 * q2);
-    const double xi = x * q2 * rq;    // x / (sqrt(1+x) + sqrt(1-x))
-    const double eta = x * q1 * rq;   // x / ((1 + sqrt(1+x)) (1 + sqrt(1-x)))
-    const double hyp = sqrt(fma(num, num, den * den));
-    const double tn = sgn1(num) * den / (fabs(num) + hyp);
-    const double c = rsqrt(fma(tn, tn, 1.0));
-    const double s = tn * c;
+    const double c = r.c, s = r.s;
     cphi = c + xi * (s - eta * c);
     cpsi = c - xi * (s + eta * c);
     const double sphi = s - xi * (c + eta * s);
     const double spsi = s + xi * (c - eta * s);
-    o.z11 = cphi * rt;
-    o.z12 = sphi * rt;
-    o.z21 = -spsi * rt;
-    o.z22 = cpsi * rt;
-    o.flags = PV_ROT;
-    bool small;
-    if (crit2)
-      small = f32cls ? (__double2float_rn(cphi) == 1.0f && __double2float_rn(cpsi) == 1.0f)
-                     : (cphi == 1.0 && cpsi == 1.0);
-    else
-      small = f32cls ? (__double2float_rn(o.z11) == 1.0f && __double2float_rn(o.z22) == 1.0f)
-                     : (o.z11 == 1.0 && o.z22 == 1.0);
-    if (!small) o.flags |= PV_BIG;
+    o.z11 = cphi * r.rt;
+    o.z12 = sphi * r.rt;
+    o.z21 = -spsi * r.rt;
+    o.z22 = cpsi * r.rt;
   }
+  o.flags = PV_ROT;
+  bool small;
+  if (crit2 && r.mode == RC_ROT)
+    small = f32cls ? (__double2float_rn(cphi) == 1.0f && __double2float_rn(cpsi) == 1.0f)
+                   : (cphi == 1.0 && cpsi == 1.0);
+  else
+    small = f32cls ? (__double2float_rn(o.z11) == 1.0f && __double2float_rn(o.z22) == 1.0f)
+                   : (o.z11 == 1.0 && o.z22 == 1.0);
+  if (!small) o.flags |= PV_BIG;
   if (sort) {
     // transformed diagonal of A-hat (Sec. 3.5.3, real case)
     const double d1 = o.z11 * o.z11 * a11 + 2.0 * o.z11 * o.z21 * a12 + o.z21 * o.z21 * a22;
@@ -171,6 +199,19 @@ __device__ __forceinline__ PivotOut pivot_real(double a11, double a22, double a1
   }
   return o;
 }
+
+// Real pivot on one thread (both chains in sequence); the same arithmetic as
+// the two-warp form, so both give identical bits.
+__device__ __forceinline__ PivotOut pivot_real(double a11, double a22, double a12, double x, double tol,
+                                               bool sort, bool f32cls, bool crit2) {
+  const RealChainA r = real_chain_a(a11, a22, a12, x, tol);
+  double xi = 0.0, eta = 0.0;
+  if (r.mode == RC_ROT) real_chain_b(x, xi, eta);
+  return real_combine(a11, a22, a12, x, r, xi, eta, sort, f32cls, crit2);
+}
+
+// Named barrier for the two parameter warps (barrier 1, 64 threads).
+__device__ __forceinline__ void param_pair_barrier() { asm volatile("bar.sync 1, 64;\n" ::: "memory"); }
 
 // Complex pivot, Sec. 2.1.1.  a12 = (ar, ai), b12 = (br, bi).
 __device__ __forceinline__ PivotOut pivot_cplx(double a11, double a22, double ar, double ai,

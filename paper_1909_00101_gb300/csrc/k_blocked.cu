@@ -111,7 +111,8 @@ __global__ void __launch_bounds__(gram_threads<T, V>()) k_gram(BlkDims d, BlkBuf
   const int m = isF ? d.mf : d.mg;
   const int nsplit = isF ? d.rf : d.rg;
   const int si = isF ? s : s - d.rf;
-  const int per = ((m + nsplit - 1) / nsplit + TR - 1) / TR * TR;
+  const int tiles = (m + TR - 1) / TR;
+  const int per = (tiles + nsplit - 1) / nsplit * TR;  // whole tiles per split
   const int r0 = si * per, r1 = min(m, r0 + per);
   const T* Y = static_cast<const T*>(isF ? b.F : b.G);
   const long long ld = isF ? b.ldf : b.ldg;
@@ -194,8 +195,18 @@ __global__ void __launch_bounds__(gram_threads<T, V>()) k_gram(BlkDims d, BlkBuf
 }
 
 // --------------------------------------------------------------- inner ----
-struct PivIn {
-  double a11, a22, ar, ai, br, bi;
+// Per-pair inputs and outputs of one inner step, in the inner data type Ti:
+// the FP64 parameter warp widens the inputs and narrows Z-hat once per pair,
+// so the pair warps never issue FP64 conversions (on sm_103a every FP64
+// instruction, conversions included, costs a full FP64 warp slot).
+template <class Ti>
+struct PivInT {
+  Ti a11, a22, ar, ai, br, bi;
+};
+template <class Ti>
+struct PivZ {
+  Ti z11, z12, z21, z22, z12i, z21i;
+  int flags;
 };
 
 // Ti: data type of the inner sweeps (double, or float in FP32 bulk sweeps);
@@ -208,11 +219,13 @@ __global__ void __launch_bounds__(512) k_inner(BlkDims d, BlkBuffers b, int step
   double* A = reinterpret_cast<double*>(smem_raw);        // E * BMAX * BMAX
   double* Bm = A + E * BMAX * BMAX;                       // E * BMAX * BMAX
   Ti* Zh = reinterpret_cast<Ti*>(Bm + E * BMAX * BMAX);   // E * BMAX * BMAX
-  PivIn* pin = reinterpret_cast<PivIn*>(Zh + E * BMAX * BMAX);
-  PivotOut* pout = reinterpret_cast<PivotOut*>(pin + BMAX / 2 + 1);
+  PivInT<Ti>* pin = reinterpret_cast<PivInT<Ti>*>(Zh + E * BMAX * BMAX);
+  PivZ<Ti>* pout = reinterpret_cast<PivZ<Ti>*>(pin + BMAX / 2 + 1);
   __shared__ int s_ctr[4];  // all, big, fail, any-change
   __shared__ double s_inv;
   __shared__ int s_bad;
+  __shared__ double s_xi[32], s_eta[32];  // chain B of the real parameters
+  __shared__ unsigned char s_pair[63][32][2];  // inner round-robin table (M - 1 steps x M / 2 pairs)
 
   const int slot = blockIdx.x;
   PairCols pc;
@@ -352,12 +365,18 @@ __global__ void __launch_bounds__(512) k_inner(BlkDims d, BlkBuffers b, int step
   const int M = bb + (bb & 1);
   const int npairs = M / 2;
   const double tol = prm.tol > 0.0 ? prm.tol : prm.eps * sqrt((double)bb);
+  for (int idx = threadIdx.x; idx < (M - 1) * npairs; idx += blockDim.x) {
+    int i, j;
+    rr_pair(M, idx / npairs, idx % npairs, i, j);
+    s_pair[idx / npairs][idx % npairs][0] = (unsigned char)i;
+    s_pair[idx / npairs][idx % npairs][1] = (unsigned char)j;
+  }
+  __syncthreads();
   for (int sw = 0; sw < prm.inner_max; ++sw) {
     int sweep_all = 0;
     for (int st = 0; st < M - 1; ++st) {
       for (int k = warp; k < npairs; k += nwarps) {
-        int i, j;
-        rr_pair(M, st, k, i, j);
+        const int i = s_pair[st][k][0], j = s_pair[st][k][1];
         if (j >= bb) continue;
         Ti v[4] = {Ti(0), Ti(0), Ti(0), Ti(0)};
         Ti w2[2] = {Ti(0), Ti(0)};
@@ -388,42 +407,80 @@ __global__ void __launch_bounds__(512) k_inner(BlkDims d, BlkBuffers b, int step
           w2[1] = warp_sum(w2[1]);
         }
         if (lane == 0) {
-          PivIn p;
+          PivInT<Ti> p;
           p.a11 = v[0]; p.a22 = v[1]; p.ar = v[2];
           if constexpr (CPLX) { p.ai = v[3]; p.br = w2[0]; p.bi = w2[1]; }
-          else { p.ai = 0.0; p.br = v[3]; p.bi = 0.0; }
+          else { p.ai = Ti(0); p.br = v[3]; p.bi = Ti(0); }
           pin[k] = p;
         }
       }
       __syncthreads();
-      // FP64 parameters, one pair per lane of warp 0 (npairs <= 32)
-      if (warp == 0 && lane < npairs) {
-        int i, j;
-        rr_pair(M, st, lane, i, j);
-        if (j < bb) {
-          const PivIn p = pin[lane];
-          PivotOut o;
-          if constexpr (CPLX)
-            o = pivot_cplx(p.a11, p.a22, p.ar, p.ai, p.br, p.bi, tol, prm.sort, prm.f32cls, prm.crit2);
-          else
-            o = pivot_real(p.a11, p.a22, p.ar, p.br, tol, prm.sort, prm.f32cls, prm.crit2);
-          pout[lane] = o;
-          if (o.flags & PV_ROT) atomicAdd(&s_ctr[0], 1);
-          if (o.flags & PV_BIG) atomicAdd(&s_ctr[1], 1);
-          if (o.flags & PV_FAIL) atomicOr(&s_ctr[2], 1);
-          if (o.flags & (PV_ROT | PV_SWAP)) atomicOr(&s_ctr[3], 1);
+      // FP64 parameters, one pair per lane (npairs <= 32); real pivots run
+      // their two independent chains on warps 0 and 1 (two SM sub-partitions),
+      // complex pivots on warp 0.  Counters are warp-aggregated.
+      if (warp <= 1) {
+        const bool act = lane < npairs && s_pair[st][lane < npairs ? lane : 0][1] < bb;
+        int fl = 0;
+        PivotOut o;
+        bool have = false;
+        if constexpr (!CPLX) {
+          if (warp == 1) {
+            double xi = 0.0, eta = 0.0;
+            if (act) real_chain_b((double)pin[lane].br, xi, eta);
+            s_xi[lane] = xi;
+            s_eta[lane] = eta;
+            param_pair_barrier();
+          } else {
+            RealChainA r;
+            double a11 = 0.0, a22 = 0.0, a12 = 0.0, x = 0.0;
+            if (act) {
+              const PivInT<Ti> p = pin[lane];
+              a11 = p.a11; a22 = p.a22; a12 = p.ar; x = p.br;
+              r = real_chain_a(a11, a22, a12, x, tol);
+            }
+            param_pair_barrier();
+            if (act) {
+              o = real_combine(a11, a22, a12, x, r, s_xi[lane], s_eta[lane], prm.sort, prm.f32cls, prm.crit2);
+              have = true;
+            }
+          }
+        } else {
+          if (warp == 0 && act) {
+            const PivInT<Ti> p = pin[lane];
+            o = pivot_cplx((double)p.a11, (double)p.a22, (double)p.ar, (double)p.ai, (double)p.br, (double)p.bi, tol,
+                           prm.sort, prm.f32cls, prm.crit2);
+            have = true;
+          }
+        }
+        if (warp == 0) {
+          if (have) {
+            PivZ<Ti> q;
+            q.z11 = (Ti)o.z11; q.z12 = (Ti)o.z12; q.z21 = (Ti)o.z21; q.z22 = (Ti)o.z22;
+            if constexpr (CPLX) { q.z12i = (Ti)o.z12i; q.z21i = (Ti)o.z21i; }
+            else { q.z12i = Ti(0); q.z21i = Ti(0); }
+            q.flags = o.flags;
+            pout[lane] = q;
+            fl = o.flags;
+          }
+          const unsigned rot = __ballot_sync(FULL, fl & PV_ROT), big = __ballot_sync(FULL, fl & PV_BIG);
+          const unsigned bad = __ballot_sync(FULL, fl & PV_FAIL), chg = __ballot_sync(FULL, fl & (PV_ROT | PV_SWAP));
+          if (lane == 0) {
+            s_ctr[0] += __popc(rot);
+            s_ctr[1] += __popc(big);
+            if (bad) s_ctr[2] = 1;
+            if (chg) s_ctr[3] = 1;
+          }
         }
       }
       __syncthreads();
       for (int k = warp; k < npairs; k += nwarps) {
-        int i, j;
-        rr_pair(M, st, k, i, j);
+        const int i = s_pair[st][k][0], j = s_pair[st][k][1];
         if (j >= bb) continue;
-        const PivotOut o = pout[k];
+        const PivZ<Ti> o = pout[k];
         const bool rot = o.flags & PV_ROT, swp = o.flags & PV_SWAP;
         if (!rot && !swp) continue;
-        const Ti z11 = (Ti)o.z11, z12 = (Ti)o.z12, z21 = (Ti)o.z21, z22 = (Ti)o.z22;
-        const Ti z12i = (Ti)o.z12i, z21i = (Ti)o.z21i;
+        const Ti z11 = o.z11, z12 = o.z12, z21 = o.z21, z22 = o.z22;
+        const Ti z12i = o.z12i, z21i = o.z21i;
         auto upd = [&](Ti* Y) {
           for (int r = lane; r < bb; r += 32) {
             if constexpr (!CPLX) {
@@ -649,7 +706,7 @@ size_t inner_smem() {
   constexpr int E = CPLX ? 2 : 1;
   constexpr int BMAX = CPLX ? V / 2 : V;
   return sizeof(double) * 2 * E * BMAX * BMAX + sizeof(Ti) * E * BMAX * BMAX +
-         sizeof(PivIn) * (BMAX / 2 + 1) + sizeof(PivotOut) * (BMAX / 2 + 1);
+         sizeof(PivInT<Ti>) * (BMAX / 2 + 1) + sizeof(PivZ<Ti>) * (BMAX / 2 + 1) + 16;
 }
 
 template <class K>

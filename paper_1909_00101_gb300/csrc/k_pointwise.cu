@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(512) k_pointwise(const PwProblem* __restrict__
   double* colnorm = reinterpret_cast<double*>(pout + table_slots);  // 2n: nf, ng
   int* ctr = reinterpret_cast<int*>(colnorm + 2 * n);               // nall, nbig, fail, rank scratch...
   int* rank = ctr + 4;
+  __shared__ double s_xi[32], s_eta[32];  // chain B of the real parameters
 
   // load (convert to T), zero Z
   const double* gF = static_cast<const double*>(P.F);
@@ -161,21 +162,56 @@ __global__ void __launch_bounds__(512) k_pointwise(const PwProblem* __restrict__
         }
       }
       __syncthreads();
-      // 2. parameters, one pair per lane
-      for (int k = threadIdx.x; k < nslots; k += blockDim.x) {
-        int i, j;
-        if (!pw_pair(prm.rowcyc, n, st, k, i, j)) continue;
-        const PivIn p = pin[k];
+      // 2. parameters, one pair per lane (nslots <= 32 for n <= 64); real
+      //    pivots run their two independent FP64 chains on warps 0 and 1,
+      //    complex pivots on warp 0; counters warp-aggregated
+      if (warp <= 1) {
+        const int k = lane;
+        int i = 0, j = 0;
+        const bool act = k < nslots && pw_pair(prm.rowcyc, n, st, k, i, j);
+        int fl = 0;
         PivotOut o;
-        if constexpr (CPLX)
-          o = pivot_cplx(p.a11, p.a22, p.ar, p.ai, p.br, p.bi, tol, prm.sort, prm.f32cls, prm.crit2);
-        else
-          o = pivot_real(p.a11, p.a22, p.ar, p.br, tol, prm.sort, prm.f32cls, prm.crit2);
-        pout[k] = o;
-        int add = (o.flags & PV_ROT) ? 1 : 0;
-        if (add) atomicAdd(&ctr[0], 1);
-        if (o.flags & PV_BIG) atomicAdd(&ctr[1], 1);
-        if (o.flags & PV_FAIL) atomicOr(&ctr[2], 1);
+        bool have = false;
+        if constexpr (!CPLX) {
+          if (warp == 1) {
+            double xi = 0.0, eta = 0.0;
+            if (act) real_chain_b(pin[k].br, xi, eta);
+            s_xi[lane] = xi;
+            s_eta[lane] = eta;
+            param_pair_barrier();
+          } else {
+            RealChainA r;
+            PivIn p{};
+            if (act) {
+              p = pin[k];
+              r = real_chain_a(p.a11, p.a22, p.ar, p.br, tol);
+            }
+            param_pair_barrier();
+            if (act) {
+              o = real_combine(p.a11, p.a22, p.ar, p.br, r, s_xi[lane], s_eta[lane], prm.sort, prm.f32cls, prm.crit2);
+              have = true;
+            }
+          }
+        } else {
+          if (warp == 0 && act) {
+            const PivIn p = pin[k];
+            o = pivot_cplx(p.a11, p.a22, p.ar, p.ai, p.br, p.bi, tol, prm.sort, prm.f32cls, prm.crit2);
+            have = true;
+          }
+        }
+        if (warp == 0) {
+          if (have) {
+            pout[k] = o;
+            fl = o.flags;
+          }
+          const unsigned rot = __ballot_sync(FULL, fl & PV_ROT), big = __ballot_sync(FULL, fl & PV_BIG);
+          const unsigned bad = __ballot_sync(FULL, fl & PV_FAIL);
+          if (lane == 0) {
+            if (rot) ctr[0] += __popc(rot);
+            if (big) ctr[1] += __popc(big);
+            if (bad) ctr[2] = 1;
+          }
+        }
       }
       __syncthreads();
       // 3. apply and swap, one warp per pair
