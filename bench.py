@@ -165,6 +165,190 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# ---------------------------------------------------------------------------
+# Other workloads (python bench.py --workload ...), one JSON line each:
+#   pointwise_real_F64x32_G48x32   latency p50/p99 of single solves on the
+#                                  pointwise in-shared-memory kernel, and the
+#                                  throughput of 1024 such solves in one call
+#   blocked_cplx_F3072x1024_G2048x1024  one complex solve, mixed vs plain FP64
+#   batched_real_512               512 real pairs (n log-uniform in [16, 256],
+#                                  m uniform in [n, 2n], seeds 1000..1511) in
+#                                  one gsvd_solve_batched call
+#   serving_poisson                a Poisson stream (n log-uniform in
+#                                  [32, 1024], m in [n, 2n], real:complex 3:1)
+#                                  through gsvd_submit/gsvd_poll: saturated
+#                                  throughput, then p50/p99 latency at 0.7x it
+# ---------------------------------------------------------------------------
+
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.asfortranarray(a)).cuda()
+
+
+def _err(sig, ref):
+    return float(np.max(np.abs(np.asarray(sig) - ref) / ref))
+
+
+def pointwise(args, hz, out):
+    import torch
+    from paper_1909_00101_gb300.inputs import make_pair, POINTWISE_64x32
+    p = make_pair(**POINTWISE_64x32)
+    F0, G0 = _dev(p.F), _dev(p.G)
+    for prec in ("fp64",):
+        with hz.Solver(path="pointwise", order="round_robin") as s:
+            for _ in range(args.warmup):
+                s.solve(F0, G0)
+            ts = []
+            for _ in range(max(args.steps, 50)):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = s.solve(F0, G0)
+                ts.append(time.perf_counter() - t0)
+            out["latency_us"] = {"p50": 1e6 * float(np.percentile(ts, 50)), "p99": 1e6 * float(np.percentile(ts, 99)),
+                                 "device_us": r.info["t_total_us"], "sweeps": r.info["sweeps_fp64"]}
+            out["accuracy"] = {"max_rel_sigma_err_vs_construction": _err(r.sigma.cpu().numpy(), p.sigma)}
+            # throughput: 1024 solves of this shape in one batched call (one CTA each)
+            pairs = [(F0, G0)] * 1024
+            s.solve_batched(pairs)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = s.solve_batched(pairs)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            out["batched_1024"] = {"solves_per_s": 1024 / dt, "ms": 1e3 * dt,
+                                   "all_ok": all(r.info["status"] == 0 for r in res)}
+    out["value"] = 1e6 / out["latency_us"]["p50"]
+    out["unit"] = "solves/s (single solve latency)"
+    out["metric"] = "GSVD solves/s and latency, pointwise 64x32"
+
+
+def complex_blocked(args, hz, out):
+    import torch
+    from paper_1909_00101_gb300.inputs import make_pair, BLOCKED_CPLX_3072x1024
+    p = make_pair(**BLOCKED_CPLX_3072x1024)
+    F0, G0 = _dev(p.F), _dev(p.G)
+    arms = {}
+    for prec in ("mixed", "fp64"):
+        with hz.Solver(path="blocked", precision=prec, inner_max_sweeps=1, max_sweeps=80, fp32_max_sweeps=80,
+                       profile=True, block_w=args.block_w or 8) as s:
+            s.solve(F0, G0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = s.solve(F0, G0)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            i = r.info
+            arms[prec] = {"s_per_solve": dt, "solves_per_s": 1 / dt, "sweeps_fp32": i["sweeps_fp32"],
+                          "sweeps_fp64": i["sweeps_fp64"], "status": i["status"], "block_w": i["block_w"],
+                          "max_rel_sigma_err_vs_construction": _err(r.sigma.cpu().numpy(), p.sigma),
+                          "kernel_ms": [round(x / 1e3, 1) for x in i["t_kernel_us"]]}
+    out["arms"] = arms
+    out["value"] = arms["mixed"]["solves_per_s"]
+    out["unit"] = "solves/s"
+    out["metric"] = "GSVD solves/s, complex 3072x1024/2048x1024, mixed vs plain FP64"
+
+
+def batched(args, hz, out):
+    import torch
+    from paper_1909_00101_gb300.inputs import make_pair, batch_shapes
+    shapes = batch_shapes(512, n_lo=16, n_hi=256, seed=0)
+    pairs = [make_pair(mf, mg, n, lo=1e-3, hi=1e3, cond=1e2, seed=1000 + k) for k, (mf, mg, n) in enumerate(shapes)]
+    dev = [(_dev(q.F), _dev(q.G)) for q in pairs]
+    arms = {}
+    for prec in ("mixed", "fp64"):
+        with hz.Solver(precision=prec, inner_max_sweeps=1, max_sweeps=80, fp32_max_sweeps=80) as s:
+            s.solve_batched(dev[:32])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = s.solve_batched(dev)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            errs = [_err(r.sigma.cpu().numpy(), q.sigma) for r, q in zip(res, pairs)]
+            per = [r.info["t_total_us"] / 1e3 for r in res]
+            arms[prec] = {"solves_per_s": 512 / dt, "s_total": dt, "ok": sum(r.info["status"] == 0 for r in res),
+                          "per_problem_ms_p50": float(np.percentile(per, 50)),
+                          "per_problem_ms_p99": float(np.percentile(per, 99)),
+                          "pointwise": sum(r.info["path"] == 1 for r in res),
+                          "max_rel_sigma_err_vs_construction": float(np.max(errs))}
+    out["arms"] = arms
+    out["value"] = arms["mixed"]["solves_per_s"]
+    out["unit"] = "solves/s"
+    out["metric"] = "GSVD solves/s, 512 real pairs n in [16, 256], mixed vs plain FP64"
+
+
+def serving(args, hz, out):
+    import torch
+    from paper_1909_00101_gb300.inputs import make_pair
+    rng = np.random.default_rng(0)
+    R = args.requests
+    pool = []
+    for k in range(min(R, 40)):
+        n = int(round(np.exp(rng.uniform(np.log(32), np.log(1024)))))
+        mf, mg = int(rng.integers(n, 2 * n + 1)), int(rng.integers(n, 2 * n + 1))
+        cplx = (k % 4 == 3)
+        pool.append(make_pair(mf, mg, n, lo=1e-4, hi=1e4, cond=1e3, cplx=cplx, seed=2000 + k))
+    dev = [(_dev(q.F), _dev(q.G)) for q in pool]
+    order = [k % len(pool) for k in range(R)]
+    arms = {}
+    for prec in ("mixed", "fp64"):
+        with hz.Solver(precision=prec, inner_max_sweeps=1, max_sweeps=80, fp32_max_sweeps=80, max_inflight=16,
+                       hbm_budget_bytes=60 << 30) as s:
+            def run(arrivals):
+                t0 = time.perf_counter()
+                pending, lat, ok, results = {}, [], 0, {}
+                k = 0
+                while k < len(arrivals) or pending:
+                    now = time.perf_counter() - t0
+                    while k < len(arrivals) and arrivals[k] <= now:
+                        F, G = dev[order[k]]
+                        t, res = s.submit(F, G)
+                        pending[t] = (k, arrivals[k], res)
+                        k += 1
+                    for t in list(pending):
+                        st, info = s.poll(t)
+                        if st != hz.EAGAIN:
+                            kk, a, res = pending.pop(t)
+                            lat.append(time.perf_counter() - t0 - a)
+                            ok += st == 0
+                            results[kk] = res
+                    time.sleep(0.0005)
+                return time.perf_counter() - t0, lat, ok, results
+            # saturation: all requests at t = 0
+            T, lat, ok, results = run([0.0] * R)
+            thr = R / T
+            errs = [_err(results[k].sigma.cpu().numpy(), pool[order[k]].sigma) for k in range(R)]
+            # Poisson arrivals at 0.7 x the saturated throughput
+            lam = 0.7 * thr
+            gaps = np.random.default_rng(1).exponential(1.0 / lam, R)
+            T2, lat2, ok2, _ = run(list(np.cumsum(gaps) - gaps[0]))
+            arms[prec] = {"saturated_solves_per_s": thr, "ok": ok,
+                          "poisson_lambda_per_s": lam, "poisson_solves_per_s": R / T2, "poisson_ok": ok2,
+                          "latency_ms_p50": 1e3 * float(np.percentile(lat2, 50)),
+                          "latency_ms_p99": 1e3 * float(np.percentile(lat2, 99)),
+                          "max_rel_sigma_err_vs_construction": float(np.max(errs))}
+    out["arms"] = arms
+    out["value"] = arms["mixed"]["poisson_solves_per_s"]
+    out["unit"] = "solves/s"
+    out["metric"] = "GSVD serving: solves/s and p50/p99 latency, Poisson arrivals, mixed vs plain FP64"
+    out["config_extra"] = {"requests": R, "distinct_pairs": len(pool), "n_range": [32, 1024], "real_to_complex": "3:1",
+                           "hbm_budget_gib": 60, "max_inflight": 16}
+
+
+def run_mode(args):
+    import torch
+    from __graft_entry__ import build
+    build()
+    import paper_1909_00101_gb300 as hz
+    torch.cuda.init()
+    out = {"workload": args.workload, "n_gpus": 1, "data": "synthetic", "higher_is_better": True}
+    fn = {"pointwise_real_F64x32_G48x32": pointwise, "blocked_cplx_F3072x1024_G2048x1024": complex_blocked,
+          "batched_real_512": batched, "serving_poisson": serving}[args.workload]
+    fn(args, hz, out)
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -179,7 +363,14 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--clocks", type=int, default=1, help="0: no nvidia-smi sampling (profiler runs)")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "pointwise_real_F64x32_G48x32", "blocked_cplx_F3072x1024_G2048x1024",
+                             "batched_real_512", "serving_poisson"])
+    ap.add_argument("--requests", type=int, default=160, help="serving: requests in the Poisson stream")
     args = ap.parse_args()
+    if args.workload != WORKLOAD and args.impl == "ours":
+        run_mode(args)
+        return
 
     if args.impl == "reference":
         if int(os.environ.get("RANK", "0")) != 0:

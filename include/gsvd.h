@@ -142,6 +142,8 @@ int gsvd_solve_batched(gsvd_handle h, const gsvd_problem *ps, int32_t count, gsv
 /* Serving: enqueue a problem (device pointers only) for the handle's
  * scheduler thread, which admits requests while the memory budget and the
  * in-flight limit allow and runs them concurrently on their own streams.
+ * The library reads the buffers on its own streams: writes to them pending
+ * on any other stream must be complete before the call.
  * Returns GSVD_OK with *ticket set, GSVD_ETOOBIG if the request alone exceeds
  * the budget, GSVD_EINVAL for a bad problem. */
 int gsvd_submit(gsvd_handle h, const gsvd_problem *p, uint64_t *ticket);

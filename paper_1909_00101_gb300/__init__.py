@@ -275,6 +275,10 @@ class Solver:
         if not dev:
             raise ValueError("submit takes device tensors")
         p = _problem(Fc, Gc, Z, sf, sg, sig, True)
+        # the copies above run on torch's stream; the library's workers read
+        # the buffers on their own streams, so they must be complete first
+        import torch
+        torch.cuda.current_stream().synchronize()
         t = ctypes.c_uint64()
         st = self._lib.gsvd_submit(self._h, ctypes.byref(p), ctypes.byref(t))
         if st != OK:

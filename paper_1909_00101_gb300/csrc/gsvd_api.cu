@@ -696,12 +696,34 @@ int gsvd_solve_batched(gsvd_handle h, const gsvd_problem* ps, int32_t count, gsv
     (P.path == GSVD_PATH_POINTWISE ? pw : blk).push_back(k);
   }
   int first = GSVD_OK;
+  // problems on the blocked path run concurrently: a pool of host workers,
+  // each with its own stream and workspace, takes problems in index order
+  // (results do not depend on which worker solves a problem)
+  std::atomic<int> next(0);
+  const int nworkers = std::min<int>((int)blk.size(), h->cfg.max_inflight);
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nworkers; ++t)
+    pool.emplace_back([&]() {
+      cudaStream_t s;
+      if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return;
+      DevBuf ws;
+      unsigned long long* hc = nullptr;
+      if (cudaMallocHost(&hc, NCTR * sizeof(unsigned long long)) == cudaSuccess) {
+        for (int q = next.fetch_add(1); q < (int)blk.size(); q = next.fetch_add(1))
+          solve_device(h->cfg, &ps[blk[q]], &loc[blk[q]], ws, hc, s);
+        cudaFreeHost(hc);
+      }
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    });
   if (!pw.empty()) {
     int st = solve_pointwise(h->cfg, ps, pw.data(), (int)pw.size(), h->stream, loc.data());
     if (st != GSVD_OK)
       for (int k : pw) loc[k].status = st;
   }
-  for (int k : blk) solve_device(h->cfg, &ps[k], &loc[k], h->ws, h->h_ctr, h->stream);
+  for (auto& t : pool) t.join();
+  for (int k : blk)
+    if (loc[k].status == GSVD_OK && loc[k].path == 0) loc[k].status = GSVD_ECUDA;  // a worker could not start
   for (int k = 0; k < count; ++k)
     if (loc[k].status != GSVD_OK && first == GSVD_OK) first = loc[k].status;
   if (infos) std::memcpy(infos, loc.data(), sizeof(gsvd_info) * count);
