@@ -219,6 +219,18 @@ def pointwise(args, hz, out):
             dt = time.perf_counter() - t0
             out["batched_1024"] = {"solves_per_s": 1024 / dt, "ms": 1e3 * dt,
                                    "all_ok": all(r.info["status"] == 0 for r in res)}
+    # the oracle on one host core, same pair
+    import oracle
+    oracle.build()
+    oracle.gsvd(p.F, p.G)
+    t0 = time.perf_counter()
+    k = 0
+    while time.perf_counter() - t0 < 3.0:
+        oracle.gsvd(p.F, p.G)
+        k += 1
+    dt = (time.perf_counter() - t0) / k
+    out["cpu_baseline"] = {"value": 1.0 / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                           "sample": "%d oracle solves of the same 64x32/48x32 pair in %.1f s" % (k, dt * k)}
     out["value"] = 1e6 / out["latency_us"]["p50"]
     out["unit"] = "solves/s (single solve latency)"
     out["metric"] = "GSVD solves/s and latency, pointwise 64x32"
@@ -250,6 +262,11 @@ def complex_blocked(args, hz, out):
     out["metric"] = "GSVD solves/s, complex 3072x1024/2048x1024, mixed vs plain FP64"
 
 
+def _oracle_status(fg):
+    import oracle
+    return oracle.gsvd(fg[0], fg[1])["status"]
+
+
 def batched(args, hz, out):
     import torch
     from paper_1909_00101_gb300.inputs import make_pair, batch_shapes
@@ -276,6 +293,19 @@ def batched(args, hz, out):
     out["value"] = arms["mixed"]["solves_per_s"]
     out["unit"] = "solves/s"
     out["metric"] = "GSVD solves/s, 512 real pairs n in [16, 256], mixed vs plain FP64"
+    # the oracle on all host cores (spawned workers), on the first 64 problems of the batch
+    import multiprocessing as mp
+    import os
+    cores = len(os.sched_getaffinity(0))
+    sample = [(q.F, q.G) for q in pairs[:64]]
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        st = pool.map(_oracle_status, sample)
+    dt = time.perf_counter() - t0
+    out["cpu_baseline"] = {"value": len(sample) / dt, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                           "sample": "the first 64 problems of the batch, %d spawned workers, %.1f s, %d ok"
+                                     % (cores, dt, sum(x == 0 for x in st))}
 
 
 def serving(args, hz, out):
@@ -470,7 +500,9 @@ def main():
     w = last["block_w"]
     b = 2 * w
     visits = sum(i["visits"] for i in infos)
-    applied = sum(i["visits_applied"] for i in infos)
+    v32 = sum(i["visits_fp32"] for i in infos)
+    applied32 = sum(i["visits_applied_fp32"] for i in infos)
+    applied64 = sum(i["visits_applied"] for i in infos) - applied32
     bf16, peak_note = measured_peaks()
     fp64_peak = bf16 * FP64_NOMINAL_TF / BF16_NOMINAL_TF
     rooflines = {}
@@ -479,14 +511,16 @@ def main():
             continue
         avg_s = tk[k] / nk[k] / 1e6
         fp32 = names[k].endswith("f32")
+        # visits per launch of this phase's kernel (FP32 bulk or FP64 sweeps)
+        ph_visits = v32 if fp32 else visits - v32
         if names[k].startswith("gram"):
-            units = visits / max(1, nk[0] + nk[3])
+            units = ph_visits / nk[k]
             flops = units * b * (b + 1) * (mf + mg)
         elif names[k].startswith("apply"):
-            units = applied / max(1, nk[2] + nk[5])
+            units = (applied32 if fp32 else applied64) / nk[k]
             flops = units * 2.0 * b * b * (mf + mg + n)
         else:
-            units = visits / max(1, nk[1] + nk[4])
+            units = ph_visits / nk[k]
             flops = units * (2.0 * b ** 3 / 3 + b * (b - 1) / 2 * 32.0 * b)
         ach = flops / avg_s / 1e12
         if fp32:

@@ -117,6 +117,8 @@ typedef struct {
   double t_kernel_us[6];    /* with profile = 1: summed launch times of Gram FP64, inner FP64, apply
                                FP64, Gram FP32, inner FP32, apply FP32 */
   int32_t n_kernel[6];      /* launch counts of the same kernels */
+  uint64_t visits_fp32;     /* of visits: those in FP32 bulk sweeps */
+  uint64_t visits_applied_fp32; /* of visits_applied: those in FP32 bulk sweeps */
 } gsvd_info;
 
 /* Fill cfg with the defaults. */

@@ -53,7 +53,8 @@ class Info(ctypes.Structure):
                 ("t_total_us", ctypes.c_double), ("t_fp32_us", ctypes.c_double), ("t_refine_us", ctypes.c_double),
                 ("block_w", ctypes.c_int32), ("chol_skipped", ctypes.c_int32),
                 ("visits", ctypes.c_uint64), ("visits_applied", ctypes.c_uint64),
-                ("t_kernel_us", ctypes.c_double * 6), ("n_kernel", ctypes.c_int32 * 6)]
+                ("t_kernel_us", ctypes.c_double * 6), ("n_kernel", ctypes.c_int32 * 6),
+                ("visits_fp32", ctypes.c_uint64), ("visits_applied_fp32", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         d = {}

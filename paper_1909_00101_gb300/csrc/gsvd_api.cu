@@ -326,6 +326,10 @@ int run_sweeps(const Plan& P, const gsvd_config& cfg, bool fp32, void* F, long l
     *chol_skipped += (int)h_ctr[3];
     info->visits += h_ctr[4];
     info->visits_applied += h_ctr[5];
+    if (fp32) {
+      info->visits_fp32 += h_ctr[4];
+      info->visits_applied_fp32 += h_ctr[5];
+    }
     if (trace) {
       const auto now = std::chrono::steady_clock::now();
       std::fprintf(stderr, "gsvd %s sweep %d: transf %llu big %llu visits %llu applied %llu fail %llu skip %llu  %.2f ms\n",

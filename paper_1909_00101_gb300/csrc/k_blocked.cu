@@ -440,7 +440,11 @@ __global__ void __launch_bounds__(512) k_inner(BlkDims d, BlkBuffers b, int step
             }
             param_pair_barrier();
             if (act) {
-              o = real_combine(a11, a22, a12, x, r, s_xi[lane], s_eta[lane], prm.sort, prm.f32cls, prm.crit2);
+              // FP32 bulk sweeps: the sort decision (a heuristic) is taken in
+              // FP32 by the pair's own warp, off this FP64 critical path
+              constexpr bool sort_here = !std::is_same<Ti, float>::value;
+              o = real_combine(a11, a22, a12, x, r, s_xi[lane], s_eta[lane], sort_here && prm.sort, prm.f32cls,
+                               prm.crit2);
               have = true;
             }
           }
@@ -477,7 +481,22 @@ __global__ void __launch_bounds__(512) k_inner(BlkDims d, BlkBuffers b, int step
         const int i = s_pair[st][k][0], j = s_pair[st][k][1];
         if (j >= bb) continue;
         const PivZ<Ti> o = pout[k];
-        const bool rot = o.flags & PV_ROT, swp = o.flags & PV_SWAP;
+        const bool rot = o.flags & PV_ROT;
+        bool swp = o.flags & PV_SWAP;
+        if constexpr (!CPLX && std::is_same<Ti, float>::value) {
+          // FP32 bulk sweeps: transformed diagonal of A-hat (Sec. 3.5.3) in FP32
+          if (prm.sort) {
+            const PivInT<Ti> p = pin[k];
+            if (rot) {
+              const float d1 = o.z11 * o.z11 * p.a11 + 2.0f * o.z11 * o.z21 * p.ar + o.z21 * o.z21 * p.a22;
+              const float d2 = o.z12 * o.z12 * p.a11 + 2.0f * o.z22 * o.z12 * p.ar + o.z22 * o.z22 * p.a22;
+              swp = d1 < d2;
+            } else if (!(o.flags & PV_FAIL)) {
+              swp = p.a11 < p.a22;
+            }
+            if (swp && lane == 0) s_ctr[3] = 1;
+          }
+        }
         if (!rot && !swp) continue;
         const Ti z11 = o.z11, z12 = o.z12, z21 = o.z21, z22 = o.z22;
         const Ti z12i = o.z12i, z21i = o.z21i;

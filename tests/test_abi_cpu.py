@@ -70,6 +70,10 @@ def test_invalid_problems_rejected_before_any_launch(lib):
     p.dtype = 7                                      # bad dtype
     assert lib.gsvd_solve(h, ctypes.byref(p), ctypes.byref(info)) == hz.EINVAL
     assert lib.gsvd_solve(h, None, ctypes.byref(info)) == hz.EINVAL
+    p.dtype = 0
+    p.n = 0                                          # empty problem
+    assert lib.gsvd_solve(h, ctypes.byref(p), ctypes.byref(info)) == hz.EINVAL
+    p.n = 4
     assert lib.gsvd_solve_batched(h, None, -1, None) == hz.EINVAL
     assert lib.gsvd_destroy(h) == 0
 

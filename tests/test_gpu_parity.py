@@ -232,3 +232,58 @@ def test_n_equal_one(hz):
     ref = oracle.gsvd(F, G)
     assert r.status == 0
     assert rel_sigma_err(_np(r.sigma), ref["sigma"]) <= 4e-16
+
+
+# ------------------------------------------------------------- full size ----
+
+def _full_size_checks(hz, p, r, n_sample=16):
+    """Properties that hold at any size, checked on the GPU in FP64, and the
+    generated sigma within n * eps * cond(X) (input rounding moves the exact
+    GSVD of the rounded pair by about eps * cond(X) per column)."""
+    F0 = _dev(p.F)
+    G0 = _dev(p.G)
+    n = p.F.shape[1]
+    U, V, Z, sf, sg, sig = r.U, r.V, r.Z, r.sigma_f, r.sigma_g, r.sigma
+    eps = 2.0 ** -53
+    assert r.status == 0, r.info
+    res_f = float(torch.linalg.norm(F0 @ Z - U * sf[None, :]) / torch.linalg.norm(F0))
+    res_g = float(torch.linalg.norm(G0 @ Z - V * sg[None, :]) / torch.linalg.norm(G0))
+    eye = torch.eye(n, dtype=U.dtype, device=U.device)
+    orth_u = float(torch.linalg.norm(U.conj().t() @ U - eye))
+    orth_v = float(torch.linalg.norm(V.conj().t() @ V - eye))
+    scale = float(torch.max(torch.abs(sf * sf + sg * sg - 1.0)))
+    s_np = sig.cpu().numpy()
+    rel = float(np.max(np.abs(s_np - p.sigma) / p.sigma))
+    print("full size: res_F %.2e res_G %.2e orth_U %.2e orth_V %.2e scale %.2e sigma err %.2e sweeps %d+%d"
+          % (res_f, res_g, orth_u, orth_v, scale, rel, r.info["sweeps_fp32"], r.info["sweeps_fp64"]))
+    assert res_f <= 1e-13 * n and res_g <= 1e-13 * n
+    assert orth_u <= 1e-12 * n and orth_v <= 1e-12 * n
+    assert scale <= 8 * eps
+    assert np.all(np.diff(s_np) <= 0)
+    assert rel <= n * eps * p.cond_x
+    # per-column backward errors of the GSVD relations on sampled columns:
+    # ||F z_j - sigma_F,j u_j|| / (||F|| ||z_j||) and likewise for G (a check
+    # through the Grams F*F, G*G would square the conditioning, App. G)
+    idx = torch.from_numpy(np.linspace(0, n - 1, n_sample).astype(np.int64)).to(Z.device)
+    zs = Z[:, idx]
+    zn = torch.linalg.norm(zs, dim=0)
+    bf = torch.linalg.norm(F0 @ zs - U[:, idx] * sf[idx][None, :], dim=0) / (torch.linalg.norm(F0, 2) * zn)
+    bg = torch.linalg.norm(G0 @ zs - V[:, idx] * sg[idx][None, :], dim=0) / (torch.linalg.norm(G0, 2) * zn)
+    assert float(torch.max(bf)) <= 8 * n * eps and float(torch.max(bg)) <= 8 * n * eps
+
+
+def test_full_size_real_4096x2048_mixed(hz):
+    """The benchmark workload in the benchmark's configuration (w = 16, BO, mixed)."""
+    from paper_1909_00101_gb300.inputs import BLOCKED_REAL_4096x2048
+    p = make_pair(**BLOCKED_REAL_4096x2048)
+    r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", precision="mixed", inner_max_sweeps=1, max_sweeps=60,
+                 fp32_max_sweeps=60)
+    _full_size_checks(hz, p, r)
+
+
+def test_full_size_complex_3072x1024_mixed(hz):
+    from paper_1909_00101_gb300.inputs import BLOCKED_CPLX_3072x1024
+    p = make_pair(**BLOCKED_CPLX_3072x1024)
+    r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", precision="mixed", block_w=8, inner_max_sweeps=1,
+                 max_sweeps=80, fp32_max_sweeps=80)
+    _full_size_checks(hz, p, r)
