@@ -170,8 +170,41 @@ __global__ void __launch_bounds__(gram_threads<T, V>()) k_gram(BlkDims d, BlkBuf
     for (int u = 0; u < NV; ++u)
 #pragma unroll
       for (int v = 0; v < NV; ++v) acc[u][v] = 0.0f;
+    // the next row tile is prefetched into registers while this one is used
+    constexpr int E = CPLX ? 2 : 1;
+    constexpr int PERT = (V / E) * TR / 256;
+    float pre[PERT][E];
+    auto fetch = [&](int rt) {
+#pragma unroll
+      for (int i = 0; i < PERT; ++i) {
+        const int idx = threadIdx.x + 256 * i, c = idx / TR, r = idx % TR;
+        pre[i][0] = 0.0f;
+        if constexpr (CPLX) pre[i][1] = 0.0f;
+        if (c < pc.bb && rt + r < r1) {
+          if constexpr (CPLX) {
+            const float2 v = reinterpret_cast<const float2*>(Y)[(size_t)pc.gcol(c) * ld + rt + r];
+            pre[i][0] = v.x;
+            pre[i][1] = v.y;
+          } else {
+            pre[i][0] = Y[(size_t)pc.gcol(c) * ld + rt + r];
+          }
+        }
+      }
+    };
+    if (r0 < r1) fetch(r0);
     for (int rt = r0; rt < r1; rt += TR) {
-      load_tile<T, CPLX, false>(Ws, LDT, Y, ld, r1, rt, pc, V);
+#pragma unroll
+      for (int i = 0; i < PERT; ++i) {
+        const int idx = threadIdx.x + 256 * i, c = idx / TR, r = idx % TR;
+        if constexpr (CPLX) {
+          const int cr = (c < pc.bb) ? c : 2 * c, ci = (c < pc.bb) ? pc.bb + c : 2 * c + 1;
+          Ws[r * LDT + cr] = pre[i][0];
+          Ws[r * LDT + ci] = pre[i][1];
+        } else {
+          Ws[r * LDT + c] = pre[i][0];
+        }
+      }
+      if (rt + TR < r1) fetch(rt + TR);
       __syncthreads();
 #pragma unroll 4
       for (int r = 0; r < TR; ++r) {
