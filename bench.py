@@ -389,6 +389,8 @@ def main():
     ap.add_argument("--block-w", type=int, default=0)
     ap.add_argument("--inner", type=int, default=1, help="inner sweep cap of the FP64 sweeps (1 = BO, 30 = FB)")
     ap.add_argument("--max-sweeps", type=int, default=60)
+    ap.add_argument("--shorten", type=int, default=1, choices=[0, 1, 2],
+                    help="QR shortening of Sec. 2: 0 never, 1 when m_F + m_G >= 2.6 n, 2 always")
     ap.add_argument("--compare", type=int, default=1, help="also time the other precision (1 step)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-baseline", type=int, default=1)
@@ -433,7 +435,7 @@ def main():
 
     def make_solver(prec, profile):
         kw = dict(precision=prec, path="blocked", profile=profile, max_sweeps=args.max_sweeps,
-                  fp32_max_sweeps=args.max_sweeps)
+                  fp32_max_sweeps=args.max_sweeps, shorten=args.shorten)
         if args.block_w:
             kw["block_w"] = args.block_w
         if args.inner:
@@ -493,12 +495,15 @@ def main():
     # pair visit (pair width b, m = m_F + m_G): Gram b(b+1) m flops, apply
     # 2 b^2 (m + n) flops per applied visit, inner 2 b^3 / 3 (two Choleskys) +
     # b(b-1)/2 pivots x 32 b flops (four dots of b, six column updates of b).
+    # With the QR shortening the sweeps run on n x n factors: m_F = m_G = n.
     names = ["gram_f64", "inner_f64", "apply_f64", "gram_f32", "inner_f32", "apply_f32"]
     tk = np.sum([i["t_kernel_us"] for i in infos], axis=0)
     nk = np.sum([i["n_kernel"] for i in infos], axis=0)
     dom = int(np.argmax(tk))
     w = last["block_w"]
     b = 2 * w
+    shortened = bool(last["shortened"])
+    sm_f, sm_g = (n, n) if shortened else (mf, mg)
     visits = sum(i["visits"] for i in infos)
     v32 = sum(i["visits_fp32"] for i in infos)
     applied32 = sum(i["visits_applied_fp32"] for i in infos)
@@ -515,10 +520,10 @@ def main():
         ph_visits = v32 if fp32 else visits - v32
         if names[k].startswith("gram"):
             units = ph_visits / nk[k]
-            flops = units * b * (b + 1) * (mf + mg)
+            flops = units * b * (b + 1) * (sm_f + sm_g)
         elif names[k].startswith("apply"):
             units = (applied32 if fp32 else applied64) / nk[k]
-            flops = units * 2.0 * b * b * (mf + mg + n)
+            flops = units * 2.0 * b * b * (sm_f + sm_g + n)
         else:
             units = ph_visits / nk[k]
             flops = units * (2.0 * b ** 3 / 3 + b * (b - 1) / 2 * 32.0 * b)
@@ -537,6 +542,19 @@ def main():
         ent.update({"kernel": names[k], "avg_launch_us": avg_s * 1e6, "launches": int(nk[k]),
                     "units_per_launch": units, "flops_per_launch": flops})
         rooflines[names[k]] = ent
+    if shortened:
+        # the QR phase (CholeskyQR2 of F and G, U = Q_F U'', V = Q_G V''),
+        # timed on the host around its launches and syncs: per m x n matrix
+        # two Grams m n^2, two Choleskys n^3 / 3, two triangular solves m n^2,
+        # R2 R1 n^3 / 3, Q U'' 2 m n^2  =>  6 m n^2 + n^3 flops
+        t_qr = sum(i["t_qr_us"] for i in infos) / len(infos) / 1e6
+        qr_flops = sum(6.0 * mm * n * n + float(n) ** 3 for mm in (mf, mg))
+        ach = qr_flops / t_qr / 1e12
+        rooflines["qr_phase_f64"] = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                                     "frac": ach / fp64_peak, "traffic": None, "kernel": "qr_phase_f64",
+                                     "phase_us": t_qr * 1e6, "flops_per_solve": qr_flops,
+                                     "launches": int(last["qr_launches"]),
+                                     "note": "whole phase incl. host syncs (two Cholesky checks)"}
     roof = dict(rooflines[names[dom]]) if nk[dom] else None
     kshare = {names[k]: round(float(tk[k] / max(1e-9, tk.sum())), 4) for k in range(6) if nk[k]}
 
@@ -545,7 +563,7 @@ def main():
            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
            "data": "synthetic",
            "config": {"workload": WORKLOAD, "m_f": mf, "m_g": mg, "n": n, "precision": args.precision,
-                      "block_w": w, "inner_max_sweeps": args.inner or 30, "sigma_range": [1e-4, 1e4],
+                      "block_w": w, "inner_max_sweeps": args.inner or 30, "shorten": args.shorten, "sigma_range": [1e-4, 1e4],
                       "cond_x": 1e3, "seed": 0, "l2": "inputs (160 MB) larger than L2"},
            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                           "min": float(np.min(step_ms))},
@@ -553,14 +571,15 @@ def main():
                         "orth_U": orth_u, "status": last["status"]},
            "solve": {k: last[k] for k in ("sweeps_fp32", "sweeps_fp64", "transf_all", "transf_big",
                                           "t_total_us", "t_fp32_us", "t_refine_us", "visits",
-                                          "visits_applied", "chol_skipped")},
+                                          "visits_applied", "chol_skipped", "shortened", "t_qr_us")},
            "kernel_time_share": kshare,
            "roofline": roof, "rooflines": rooflines, "clocks": clk,
            "gpu_launches": None}
     # launches of our kernels in the timed region: per sweep 3 per outer step
     # plus prescale/rescale/finalize/check kernels
     out["gpu_launches"] = int(sum(sum(i["n_kernel"]) for i in infos)
-                              + args.steps * 14 + sum(i["sweeps_fp32"] + i["sweeps_fp64"] for i in infos))
+                              + args.steps * 14 + sum(i["sweeps_fp32"] + i["sweeps_fp64"] for i in infos)
+                              + sum(i["qr_launches"] for i in infos))
 
     if args.compare and rank == 0:
         other = "fp64" if args.precision == "mixed" else "mixed"

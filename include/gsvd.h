@@ -80,7 +80,10 @@ typedef struct {
                                solve's stream (gsvd_info.t_kernel_us); 0 = off (default) */
   int32_t inner_max_sweeps_fp32; /* inner sweep cap of the FP32 bulk sweeps (default 1 = BO;
                                0 = same as inner_max_sweeps) */
-  int32_t reserved;
+  int32_t shorten;          /* QR shortening of Sec. 2 (F = Q_F R_F, G = Q_G R_G, sweeps on the n x n
+                               factors): 0 = never, 1 = when m_F + m_G >= 2.6 n on the blocked real path
+                               (default), 2 = whenever possible.  Skipped (and reported) when a Gram of
+                               F or G is too ill-conditioned for CholeskyQR2 */
 } gsvd_config;
 
 /* One problem.  dtype = GSVD_R64 or GSVD_C128. */
@@ -119,6 +122,11 @@ typedef struct {
   int32_t n_kernel[6];      /* launch counts of the same kernels */
   uint64_t visits_fp32;     /* of visits: those in FP32 bulk sweeps */
   uint64_t visits_applied_fp32; /* of visits_applied: those in FP32 bulk sweeps */
+  int32_t shortened;        /* 1: the sweeps ran on the QR factors (R_F, R_G) */
+  int32_t shorten_skipped;  /* 1: shortening was wanted but a Gram was too ill-conditioned */
+  double t_qr_us;           /* time of the QR shortening and of U = Q_F U'', V = Q_G V'' */
+  int32_t qr_launches;      /* kernel launches of the QR shortening (CholeskyQR2 and the products) */
+  int32_t reserved2;
 } gsvd_info;
 
 /* Fill cfg with the defaults. */

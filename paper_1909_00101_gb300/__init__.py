@@ -37,7 +37,7 @@ class Config(ctypes.Structure):
                 ("path", ctypes.c_int32), ("order", ctypes.c_int32), ("fp32_max_sweeps", ctypes.c_int32),
                 ("timeout_ms", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_uint64),
                 ("max_inflight", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("inner_max_sweeps_fp32", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("inner_max_sweeps_fp32", ctypes.c_int32), ("shorten", ctypes.c_int32)]
 
 
 class Problem(ctypes.Structure):
@@ -54,7 +54,9 @@ class Info(ctypes.Structure):
                 ("block_w", ctypes.c_int32), ("chol_skipped", ctypes.c_int32),
                 ("visits", ctypes.c_uint64), ("visits_applied", ctypes.c_uint64),
                 ("t_kernel_us", ctypes.c_double * 6), ("n_kernel", ctypes.c_int32 * 6),
-                ("visits_fp32", ctypes.c_uint64), ("visits_applied_fp32", ctypes.c_uint64)]
+                ("visits_fp32", ctypes.c_uint64), ("visits_applied_fp32", ctypes.c_uint64),
+                ("shortened", ctypes.c_int32), ("shorten_skipped", ctypes.c_int32), ("t_qr_us", ctypes.c_double),
+                ("qr_launches", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         d = {}
@@ -107,7 +109,7 @@ def strerror(status: int) -> str:
 
 def make_config(precision="fp64", block_w=0, max_sweeps=30, inner_max_sweeps=30, criterion=1, sort=True,
                 path="auto", order="round_robin", fp32_max_sweeps=30, hbm_budget_bytes=60 << 30,
-                max_inflight=16, profile=False, inner_max_sweeps_fp32=1) -> Config:
+                max_inflight=16, profile=False, inner_max_sweeps_fp32=1, shorten=1) -> Config:
     c = Config()
     load_library().gsvd_config_default(ctypes.byref(c))
     c.precision = PREC[precision]
@@ -123,6 +125,7 @@ def make_config(precision="fp64", block_w=0, max_sweeps=30, inner_max_sweeps=30,
     c.max_inflight = max_inflight
     c.profile = 1 if profile else 0
     c.inner_max_sweeps_fp32 = inner_max_sweeps_fp32
+    c.shorten = shorten
     return c
 
 

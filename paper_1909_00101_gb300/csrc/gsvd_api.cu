@@ -413,9 +413,33 @@ int solve_pointwise(const gsvd_config& cfg, const gsvd_problem* ps, const int* i
   return GSVD_OK;
 }
 
+// QR shortening applies to real blocked problems that are tall enough
+bool shorten_applies(const gsvd_config& cfg, const Plan& P, int64_t mf, int64_t mg, int64_t n) {
+  return P.path == GSVD_PATH_BLOCKED && !P.cplx && n >= 2 &&
+         (cfg.shorten == 2 || (cfg.shorten == 1 && (double)(mf + mg) >= 2.6 * (double)n));
+}
+
+// workspace of a shortened solve: the n x n sub-problem's plan, then
+// R_F, R_G, R1_F, R1_G (n x n each), a max(m_F, m_G) x n product buffer and
+// two flags
+size_t shortened_offset(const gsvd_config& cfg, int64_t n) {
+  Plan S;
+  make_plan(cfg, GSVD_R64, n, n, n, S);
+  return (S.total + 255) & ~size_t(255);
+}
+size_t shortened_total(const gsvd_config& cfg, int64_t mf, int64_t mg, int64_t n) {
+  return shortened_offset(cfg, n) + sizeof(double) * (4 * (size_t)n * n + (size_t)std::max(mf, mg) * n) + 256;
+}
+
+// device bytes one solve needs
+size_t solve_bytes(const gsvd_config& cfg, const Plan& P, int64_t mf, int64_t mg, int64_t n) {
+  if (shorten_applies(cfg, P, mf, mg, n)) return std::max(P.total, shortened_total(cfg, mf, mg, n));
+  return P.total;
+}
+
 // one problem with device pointers on stream s, workspace ws (>= P.total)
-int solve_device(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info, DevBuf& ws,
-                 unsigned long long* h_ctr, cudaStream_t s) {
+int solve_plain(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info, DevBuf& ws,
+                unsigned long long* h_ctr, cudaStream_t s) {
   Plan P;
   if (!make_plan(cfg, p->dtype, p->m_f, p->m_g, p->n, P)) return GSVD_EINVAL;
   CK(ws.ensure(P.total));
@@ -509,6 +533,110 @@ int solve_device(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info,
   info->t_refine_us = cfg.precision == GSVD_PREC_MIXED ? ms_64 * 1e3 : 0.0;
   info->status = status;
   return status;
+}
+
+constexpr int SHORT_SKIP = 100;
+
+// QR shortening (Sec. 2): F = Q_F R_F, G = Q_G R_G by CholeskyQR2, the sweeps
+// on (R_F, R_G) (n x n), then U = Q_F U'', V = Q_G V''.  Returns SHORT_SKIP,
+// with F and G untouched, when a first Cholesky fails (too ill-conditioned).
+int solve_shortened(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info, DevBuf& ws,
+                    unsigned long long* h_ctr, cudaStream_t s) {
+  const int n = (int)p->n, mf = (int)p->m_f, mg = (int)p->m_g;
+  double* F = (double*)p->F;
+  double* G = (double*)p->G;
+  const size_t nn = (size_t)n * n;
+  const size_t tmp = (size_t)std::max(mf, mg) * n;
+  CK(ws.ensure(shortened_total(cfg, mf, mg, n)));
+  double* RF = reinterpret_cast<double*>(static_cast<unsigned char*>(ws.p) + shortened_offset(cfg, n));
+  double* RG = RF + nn;
+  double* R1F = RG + nn;
+  double* R1G = R1F + nn;
+  double* T = R1G + nn;
+  int* flag = reinterpret_cast<int*>(T + tmp);
+  int hflag[2];
+  const long long l0 = qr_launch_count();
+  CK(cudaMemsetAsync(flag, 0, 8, s));
+  CK(launch_check_finite(mf, n, false, F, p->ldf, flag + 1, s));
+  CK(launch_check_finite(mg, n, false, G, p->ldg, flag + 1, s));
+  // first pass: Grams and Choleskys; F and G are not modified yet
+  CK(dgemm(true, false, n, n, mf, 1.0, F, p->ldf, F, p->ldf, 0.0, R1F, n, true, s));
+  CK(potrf_upper(n, R1F, n, flag, s));
+  CK(dgemm(true, false, n, n, mg, 1.0, G, p->ldg, G, p->ldg, 0.0, R1G, n, true, s));
+  CK(potrf_upper(n, R1G, n, flag, s));
+  CK(cudaMemcpyAsync(hflag, flag, 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (hflag[1]) return GSVD_EINVAL;
+  if (hflag[0]) {
+    info->shorten_skipped = 1;
+    return SHORT_SKIP;
+  }
+  // Q1 = F R1^{-1}; second pass R2 = chol(Q1^T Q1), Q = Q1 R2^{-1}
+  CK(trsm_right_upper(mf, n, R1F, n, F, p->ldf, s));
+  CK(trsm_right_upper(mg, n, R1G, n, G, p->ldg, s));
+  CK(dgemm(true, false, n, n, mf, 1.0, F, p->ldf, F, p->ldf, 0.0, RF, n, true, s));
+  CK(potrf_upper(n, RF, n, flag, s));
+  CK(dgemm(true, false, n, n, mg, 1.0, G, p->ldg, G, p->ldg, 0.0, RG, n, true, s));
+  CK(potrf_upper(n, RG, n, flag, s));
+  CK(cudaMemcpyAsync(hflag, flag, 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (hflag[0]) {
+    // Q1^T Q1 not numerically positive definite: undo (F = Q1 R1) and skip
+    CK(dgemm(false, false, mf, n, n, 1.0, F, p->ldf, R1F, n, 0.0, T, mf, false, s));
+    CK(cudaMemcpy2DAsync(F, p->ldf * 8, T, (size_t)mf * 8, (size_t)mf * 8, n, cudaMemcpyDeviceToDevice, s));
+    CK(dgemm(false, false, mg, n, n, 1.0, G, p->ldg, R1G, n, 0.0, T, mg, false, s));
+    CK(cudaMemcpy2DAsync(G, p->ldg * 8, T, (size_t)mg * 8, (size_t)mg * 8, n, cudaMemcpyDeviceToDevice, s));
+    info->shorten_skipped = 1;
+    return SHORT_SKIP;
+  }
+  CK(trsm_right_upper(mf, n, RF, n, F, p->ldf, s));
+  CK(trsm_right_upper(mg, n, RG, n, G, p->ldg, s));
+  // R = R2 R1 (both upper triangular)
+  CK(dgemm(false, false, n, n, n, 1.0, RF, n, R1F, n, 0.0, T, n, 2, s));
+  CK(launch_zero_lower(n, T, n, s));
+  CK(cudaMemcpyAsync(RF, T, nn * 8, cudaMemcpyDeviceToDevice, s));
+  CK(dgemm(false, false, n, n, n, 1.0, RG, n, R1G, n, 0.0, T, n, 2, s));
+  CK(launch_zero_lower(n, T, n, s));
+  CK(cudaMemcpyAsync(RG, T, nn * 8, cudaMemcpyDeviceToDevice, s));
+  // the sweeps on the shortened pair
+  gsvd_problem sub = *p;
+  sub.m_f = n;
+  sub.m_g = n;
+  sub.F = RF;
+  sub.ldf = n;
+  sub.G = RG;
+  sub.ldg = n;
+  gsvd_config c2 = cfg;
+  c2.shorten = 0;
+  const int st = solve_plain(c2, &sub, info, ws, h_ctr, s);
+  if (st == GSVD_EINVAL || st == GSVD_ECUDA || st == GSVD_ENOMEM) return st;
+  // U = Q_F U'', V = Q_G V''
+  CK(dgemm(false, false, mf, n, n, 1.0, F, p->ldf, RF, n, 0.0, T, mf, false, s));
+  CK(cudaMemcpy2DAsync(F, p->ldf * 8, T, (size_t)mf * 8, (size_t)mf * 8, n, cudaMemcpyDeviceToDevice, s));
+  CK(dgemm(false, false, mg, n, n, 1.0, G, p->ldg, RG, n, 0.0, T, mg, false, s));
+  CK(cudaMemcpy2DAsync(G, p->ldg * 8, T, (size_t)mg * 8, (size_t)mg * 8, n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  info->shortened = 1;
+  info->qr_launches = (int32_t)(qr_launch_count() - l0 + 2);  // + the two finiteness checks
+  return st;
+}
+
+int solve_device(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info, DevBuf& ws,
+                 unsigned long long* h_ctr, cudaStream_t s) {
+  Plan P;
+  if (!make_plan(cfg, p->dtype, p->m_f, p->m_g, p->n, P)) return GSVD_EINVAL;
+  if (shorten_applies(cfg, P, p->m_f, p->m_g, p->n)) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const int st = solve_shortened(cfg, p, info, ws, h_ctr, s);
+    if (st != SHORT_SKIP) {
+      const double us = std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count();
+      info->t_qr_us = us - info->t_total_us;
+      info->t_total_us = us;
+      info->status = st;
+      return st;
+    }
+  }
+  return solve_plain(cfg, p, info, ws, h_ctr, s);
 }
 
 // host pointers: stage through device buffers (pinned or pageable host memory)
@@ -621,6 +749,7 @@ void gsvd_config_default(gsvd_config* c) {
   c->max_inflight = 16;
   c->profile = 0;
   c->inner_max_sweeps_fp32 = 1;
+  c->shorten = 1;
 }
 
 int gsvd_create(gsvd_handle* h, const gsvd_config* cfg, void* stream) {
@@ -742,7 +871,7 @@ uint64_t gsvd_workspace_bytes(const gsvd_config* cfg, int32_t dtype, int64_t mf,
     gsvd_config_default(&c);
   Plan P;
   if (!make_plan(c, dtype, mf, mg, n, P)) return 0;
-  return P.total;
+  return solve_bytes(c, P, mf, mg, n);
 }
 
 int gsvd_submit(gsvd_handle h, const gsvd_problem* p, uint64_t* ticket) {
@@ -752,7 +881,7 @@ int gsvd_submit(gsvd_handle h, const gsvd_problem* p, uint64_t* ticket) {
   if (!(is_device_ptr(p->F) && is_device_ptr(p->G) && is_device_ptr(p->Z))) return GSVD_EINVAL;
   Plan P;
   if (!make_plan(h->cfg, p->dtype, p->m_f, p->m_g, p->n, P)) return GSVD_EINVAL;
-  const uint64_t bytes = P.total;
+  const uint64_t bytes = solve_bytes(h->cfg, P, p->m_f, p->m_g, p->n);
   if (bytes > h->cfg.hbm_budget_bytes) return GSVD_ETOOBIG;
   std::unique_ptr<Request> r(new Request);
   r->prob = *p;

@@ -114,6 +114,20 @@ cudaError_t launch_gemm_f64_by_f32(int m, int n, bool cplx, const double* A, lon
 // Z64 = diag(zdiag) * Z32 (rows scaled), FP64 result
 cudaError_t launch_rowscale(int n, bool cplx, const double* zdiag, const float* Z32, long long ld32,
                             double* Z, long long ldz, cudaStream_t s);
+// FP64 DMMA GEMM: C = alpha op(A) op(B) + beta C (column-major); upper = 1:
+// only tiles meeting C's upper triangle are computed; upper = 2: also op(A)
+// and op(B) are upper triangular (square), so each tile sums its k range only
+cudaError_t dgemm(bool ta, bool tb, int M, int N, int K, double alpha, const double* A, long long lda,
+                  const double* B, long long ldb, double beta, double* C, long long ldc, int upper,
+                  cudaStream_t s);
+// kernels launched so far by the calling thread's dgemm/potrf/trsm calls
+long long qr_launch_count();
+// zero the strict lower triangle of an n x n matrix
+cudaError_t launch_zero_lower(int n, double* A, long long lda, cudaStream_t s);
+// blocked Cholesky A = R^T R in place (upper), *fail = 1 on a non-positive pivot
+cudaError_t potrf_upper(int n, double* A, long long lda, int* fail, cudaStream_t s);
+// B (m x n) <- B R^{-1} for upper triangular R (n x n)
+cudaError_t trsm_right_upper(int m, int n, const double* R, long long ldr, double* B, long long ldb, cudaStream_t s);
 // non-finite check of a column-major matrix: sets *flag = 1 on NaN/Inf
 cudaError_t launch_check_finite(int m, int n, bool cplx, const double* A, long long lda, int* flag,
                                 cudaStream_t s);

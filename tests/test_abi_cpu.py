@@ -89,10 +89,19 @@ def test_bad_config_rejected(lib):
 
 def test_workspace_bytes_grows_with_size(lib):
     import paper_1909_00101_gb300 as hz
-    cfg = hz.make_config(path="blocked")
+    cfg = hz.make_config(path="blocked", shorten=0)
     a = lib.gsvd_workspace_bytes(ctypes.byref(cfg), 0, 512, 512, 256)
     b = lib.gsvd_workspace_bytes(ctypes.byref(cfg), 0, 4096, 4096, 2048)
     c = lib.gsvd_workspace_bytes(ctypes.byref(cfg), 1, 4096, 4096, 2048)
     assert 0 < a < b < c
-    mixed = hz.make_config(path="blocked", precision="mixed")
+    mixed = hz.make_config(path="blocked", precision="mixed", shorten=0)
     assert lib.gsvd_workspace_bytes(ctypes.byref(mixed), 0, 4096, 4096, 2048) > b
+    # QR shortening (real, tall): the n x n sub-problem's workspace plus
+    # R_F, R_G, R1_F, R1_G (n^2 each) and a max(m_F, m_G) x n product buffer
+    sh = hz.make_config(path="blocked", shorten=1)
+    n, m = 2048, 4096
+    sub = lib.gsvd_workspace_bytes(ctypes.byref(cfg), 0, n, n, n)
+    got = lib.gsvd_workspace_bytes(ctypes.byref(sh), 0, m, m, n)
+    assert got >= sub + 8 * (4 * n * n + m * n) and got <= sub + 8 * (4 * n * n + m * n) + 1024
+    # complex problems are not shortened
+    assert lib.gsvd_workspace_bytes(ctypes.byref(sh), 1, m, m, n) == c

@@ -100,14 +100,16 @@ def test_pointwise_complex(hz):
 
 # -------------------------------------------------------------- blocked ----
 
+@pytest.mark.parametrize("shorten", [0, 2])
 @pytest.mark.parametrize("w,shape", [(8, (160, 130, 96)), (16, (200, 180, 100)), (32, (300, 257, 150)),
                                      (8, (70, 65, 61))])
-def test_blocked_real_fp64(hz, w, shape):
+def test_blocked_real_fp64(hz, w, shape, shorten):
     mf, mg, n = shape
     p = make_pair(mf, mg, n, lo=1e-3, hi=1e3, cond=1e2, seed=w + n)
-    r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", block_w=w)
+    r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", block_w=w, shorten=shorten)
     assert r.info["path"] == 2 and r.info["block_w"] == w
-    check(p.F, p.G, r, label="blocked w=%d %s" % (w, shape))
+    assert r.info["shortened"] == (1 if shorten else 0), r.info
+    check(p.F, p.G, r, label="blocked w=%d %s shorten=%d" % (w, shape, shorten))
 
 
 @pytest.mark.parametrize("w", [4, 8, 16])
@@ -115,6 +117,60 @@ def test_blocked_complex_fp64(hz, w):
     p = make_pair(120, 90, 72, lo=1e-3, hi=1e3, cond=1e2, cplx=True, seed=w)
     r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", block_w=w)
     check(p.F, p.G, r, label="blocked-complex w=%d" % w)
+
+
+# QR shortening (Sec. 2): the sweeps run on the n x n triangular factors
+
+@pytest.mark.parametrize("shape", [(512, 400, 160), (333, 1000, 97), (2000, 150, 129)])
+def test_shortened_matches_oracle(hz, shape):
+    """Tall pairs, ragged n (not a multiple of the 32-column Cholesky and
+    triangular-solve blocks nor of the 64 x 64 GEMM tiles); default shorten."""
+    mf, mg, n = shape
+    p = make_pair(mf, mg, n, lo=1e-3, hi=1e3, cond=1e2, seed=n)
+    r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", block_w=8)
+    assert r.info["shortened"] == 1 and r.info["shorten_skipped"] == 0, r.info
+    check(p.F, p.G, r, label="shortened %s" % (shape,))
+
+
+def test_shortened_mixed(hz):
+    p = make_pair(700, 600, 192, lo=1e-4, hi=1e4, cond=1e3, seed=31)
+    r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", block_w=16, precision="mixed", inner_max_sweeps=1,
+                 max_sweeps=60, fp32_max_sweeps=60)
+    assert r.info["shortened"] == 1 and r.info["sweeps_fp32"] >= 1, r.info
+    check(p.F, p.G, r, label="shortened mixed")
+
+
+def test_shortened_equals_unshortened_within_tolerance(hz):
+    """Both orders of work give the same GSVD to the FP64 tolerance; the
+    right vectors Z agree column by column up to sign."""
+    p = make_pair(600, 500, 128, lo=1e-2, hi=1e2, cond=1e2, seed=8)
+    a = hz.solve(_dev(p.F), _dev(p.G), path="blocked", block_w=16, shorten=0)
+    b = hz.solve(_dev(p.F), _dev(p.G), path="blocked", block_w=16, shorten=2)
+    assert a.info["shortened"] == 0 and b.info["shortened"] == 1
+    assert rel_sigma_err(_np(b.sigma), _np(a.sigma)) <= 1e-12
+    za, zb = _np(a.Z), _np(b.Z)
+    sgn = np.sign(np.sum(za * zb, axis=0))
+    assert np.max(np.abs(za - zb * sgn[None, :])) / np.max(np.abs(za)) <= 1e-9
+
+
+def test_shorten_skipped_on_singular_gram(hz):
+    """A zero column of G makes G^T G singular: the first Cholesky meets an
+    exact zero pivot, the solve falls back to the unshortened sweeps with F
+    and G untouched, and those report G rank deficient."""
+    p = make_pair(400, 300, 96, seed=41)
+    G = p.G.copy(order="F")
+    G[:, 5] = 0.0
+    r = hz.solve(_dev(p.F), _dev(G), path="blocked", block_w=8, shorten=2)
+    assert r.info["shortened"] == 0 and r.info["shorten_skipped"] == 1, r.info
+    assert r.status == hz.ENOTPD
+
+
+def test_shortened_bitwise_repeatable(hz):
+    p = make_pair(500, 450, 100, seed=9)
+    a = hz.solve(_dev(p.F), _dev(p.G), path="blocked", block_w=8, shorten=2)
+    b = hz.solve(_dev(p.F), _dev(p.G), path="blocked", block_w=8, shorten=2)
+    for x, y in ((a.U, b.U), (a.V, b.V), (a.Z, b.Z), (a.sigma, b.sigma)):
+        assert torch.equal(x, y)
 
 
 def test_blocked_bo_inner_one_sweep(hz):
@@ -209,7 +265,7 @@ def test_status_rank_deficient_G(hz, path):
     G[:, 5] = 0.0
     G[:4, 5] = 1.0
     G[:, 6] = G[:, 5]
-    r = hz.solve(_dev(p.F), _dev(G), path=path, block_w=4 if path == "blocked" else 0)
+    r = hz.solve(_dev(p.F), _dev(G), path=path, block_w=4 if path == "blocked" else 0, shorten=0)
     assert r.status == hz.ENOTPD
 
 
@@ -279,9 +335,20 @@ def test_full_size_real_4096x2048_mixed(hz):
     r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", precision="mixed", inner_max_sweeps=1, max_sweeps=60,
                  fp32_max_sweeps=60)
     _full_size_checks(hz, p, r)
+    assert r.info["shortened"] == 1, r.info
     # the FP32 bulk sweeps converge on their own (FP32 Gram/apply are right)
     # and leave few FP64 sweeps
     assert r.info["sweeps_fp32"] < 60 and r.info["sweeps_fp64"] <= 15, r.info
+
+
+def test_full_size_real_4096x2048_unshortened(hz):
+    """The same workload without the QR shortening (every sweep on 4096 rows)."""
+    from paper_1909_00101_gb300.inputs import BLOCKED_REAL_4096x2048
+    p = make_pair(**BLOCKED_REAL_4096x2048)
+    r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", precision="mixed", inner_max_sweeps=1, max_sweeps=60,
+                 fp32_max_sweeps=60, shorten=0)
+    _full_size_checks(hz, p, r)
+    assert r.info["shortened"] == 0, r.info
 
 
 def test_full_size_complex_3072x1024_mixed(hz):
