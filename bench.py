@@ -138,6 +138,14 @@ def oracle_sample(F, G, n, budget_s=10.0):
             "est_seconds_per_solve": t_solve}
 
 
+def lib_kw(args) -> dict:
+    """Library options given on the command line (else the library's defaults)."""
+    kw = {}
+    if getattr(args, "fp32_params", None) is not None:
+        kw["fp32_params"] = args.fp32_params
+    return kw
+
+
 def run_reference(args):
     """The oracle as it stands, on the host cores, on this workload (bounded samples)."""
     from paper_1909_00101_gb300.inputs import make_pair, BLOCKED_REAL_4096x2048
@@ -244,7 +252,7 @@ def complex_blocked(args, hz, out):
     arms = {}
     for prec in ("mixed", "fp64"):
         with hz.Solver(path="blocked", precision=prec, inner_max_sweeps=1, max_sweeps=80, fp32_max_sweeps=80,
-                       profile=True, block_w=args.block_w or 8) as s:
+                       profile=True, block_w=args.block_w or 8, **lib_kw(args)) as s:
             s.solve(F0, G0)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -275,7 +283,7 @@ def batched(args, hz, out):
     dev = [(_dev(q.F), _dev(q.G)) for q in pairs]
     arms = {}
     for prec in ("mixed", "fp64"):
-        with hz.Solver(precision=prec, inner_max_sweeps=1, max_sweeps=80, fp32_max_sweeps=80) as s:
+        with hz.Solver(precision=prec, inner_max_sweeps=1, max_sweeps=80, fp32_max_sweeps=80, **lib_kw(args)) as s:
             s.solve_batched(dev[:32])
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -324,7 +332,7 @@ def serving(args, hz, out):
     arms = {}
     for prec in ("mixed", "fp64"):
         with hz.Solver(precision=prec, inner_max_sweeps=1, max_sweeps=80, fp32_max_sweeps=80, max_inflight=16,
-                       hbm_budget_bytes=60 << 30) as s:
+                       hbm_budget_bytes=60 << 30, **lib_kw(args)) as s:
             def run(arrivals):
                 t0 = time.perf_counter()
                 pending, lat, ok, results = {}, [], 0, {}
@@ -389,6 +397,8 @@ def main():
     ap.add_argument("--block-w", type=int, default=0)
     ap.add_argument("--inner", type=int, default=1, help="inner sweep cap of the FP64 sweeps (1 = BO, 30 = FB)")
     ap.add_argument("--max-sweeps", type=int, default=60)
+    ap.add_argument("--fp32-params", type=int, default=None, choices=[0, 1],
+                    help="2x2 parameters of the FP32 bulk sweeps in FP32 (1) or FP64 (0); default: library's")
     ap.add_argument("--shorten", type=int, default=1, choices=[0, 1, 2],
                     help="QR shortening of Sec. 2: 0 never, 1 when m_F + m_G >= 2.6 n, 2 always")
     ap.add_argument("--compare", type=int, default=1, help="also time the other precision (1 step)")
@@ -436,6 +446,7 @@ def main():
     def make_solver(prec, profile):
         kw = dict(precision=prec, path="blocked", profile=profile, max_sweeps=args.max_sweeps,
                   fp32_max_sweeps=args.max_sweeps, shorten=args.shorten)
+        kw.update(lib_kw(args))
         if args.block_w:
             kw["block_w"] = args.block_w
         if args.inner:

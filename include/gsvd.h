@@ -84,6 +84,9 @@ typedef struct {
                                factors): 0 = never, 1 = when m_F + m_G >= 2.6 n on the blocked real path
                                (default), 2 = whenever possible.  Skipped (and reported) when a Gram of
                                F or G is too ill-conditioned for CholeskyQR2 */
+  int32_t fp32_params;      /* mixed precision: 1 = the pivot-pair step of the FP32 bulk sweeps (partial
+                               Gram sums, the two Choleskys, the 2x2 parameters) in FP32, whose inputs
+                               are FP32 dot products anyway (default); 0 = those in FP64 */
 } gsvd_config;
 
 /* One problem.  dtype = GSVD_R64 or GSVD_C128. */

@@ -299,6 +299,7 @@ int run_sweeps(const Plan& P, const gsvd_config& cfg, bool fp32, void* F, long l
   ip.f32cls = fp32;
   ip.crit2 = cfg.criterion == 2;
   ip.chol_skip = fp32;
+  ip.par32 = fp32 && cfg.fp32_params != 0;
   int sw = 0;
   bool converged = false;
   const bool prof = cfg.profile != 0;
@@ -750,6 +751,7 @@ void gsvd_config_default(gsvd_config* c) {
   c->profile = 0;
   c->inner_max_sweeps_fp32 = 1;
   c->shorten = 1;
+  c->fp32_params = 1;
 }
 
 int gsvd_create(gsvd_handle* h, const gsvd_config* cfg, void* stream) {

@@ -1,6 +1,6 @@
 // hz_device.cuh -- device-side building blocks of the implicit Hari-Zimmermann
-// GSVD sweep engine for sm_103a: deterministic warp reductions, the FP64 2x2
-// transformation parameters (real and complex), and small helpers.
+// GSVD sweep engine for sm_103a: deterministic warp reductions, the 2x2
+// transformation parameters (real and complex, FP64 or FP32), and small helpers.
 //
 // Paper: Novakovic & Singer, "Implicit Hari-Zimmermann algorithm for the
 // generalized SVD on the GPUs" (arXiv 1909.00101).
@@ -68,30 +68,49 @@ __device__ __forceinline__ void warp_sum4(T v[4]) {
   v[3] = __shfl_sync(FULL, k, 24);
 }
 
+// Scalar helpers overloaded on double and float, so that the 2x2 parameters
+// below can run in either precision with the same expression order.
 __device__ __forceinline__ double sgn1(double y) { return copysign(1.0, y); }
+__device__ __forceinline__ float sgn1(float y) { return copysignf(1.0f, y); }
+__device__ __forceinline__ double p_rsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float p_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double p_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float p_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double p_hypot(double x, double y) { return hypot(x, y); }
+__device__ __forceinline__ float p_hypot(float x, float y) { return hypotf(x, y); }
+__device__ __forceinline__ double p_abs(double x) { return fabs(x); }
+__device__ __forceinline__ float p_abs(float x) { return fabsf(x); }
+__device__ __forceinline__ double p_fma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float p_fma(float a, float b, float c) { return fmaf(a, b, c); }
+// "rounds to 1 in FP32" (the small-transformation class of the FP32 sweeps)
+__device__ __forceinline__ bool f32_is_one(double x) { return __double2float_rn(x) == 1.0f; }
+__device__ __forceinline__ bool f32_is_one(float x) { return x == 1.0f; }
 
 // cos and sin from tan of an angle in (-pi/2, pi/2]; tan = +-inf gives
 // cos = 0, sin = +-1 (IEEE signed division decides the sign).
-__device__ __forceinline__ void trig_from_tan(double tn, double& c, double& s) {
+template <class T>
+__device__ __forceinline__ void trig_from_tan(T tn, T& c, T& s) {
   if (isinf(tn)) {
-    c = 0.0;
+    c = T(0);
     s = sgn1(tn);
   } else {
-    c = rsqrt(fma(tn, tn, 1.0));
+    c = p_rsqrt(p_fma(tn, tn, T(1)));
     s = tn * c;
   }
 }
 
 // Result of one 2x2 pivot: Z-hat (row-major), imaginary parts of the two
 // off-diagonal entries for complex pivots (the diagonal is real), and flags.
-struct PivotOut {
-  double z11, z12, z21, z22;
-  double z12i, z21i;
+template <class T>
+struct PivotOutT {
+  T z11, z12, z21, z22;
+  T z12i, z21i;
   int flags;  // PV_* bits
 };
+using PivotOut = PivotOutT<double>;
 enum : int { PV_ROT = 1, PV_BIG = 2, PV_SWAP = 4, PV_FAIL = 8 };
 
-// Real pivot, Sec. 2.1.2, in two independent FP64 chains that can run on two
+// Real pivot, Sec. 2.1.2, in two independent chains that can run on two
 // warps (two SM sub-partitions) at once -- on sm_103a a lone warp issues one
 // FP64 instruction per ~76 cycles, so the chain length sets the step latency:
 //   chain A: skip test, t = sqrt(1 - x^2) (with 1/t), cot 2theta as num/den,
@@ -104,58 +123,73 @@ enum : int { PV_ROT = 1, PV_BIG = 2, PV_SWAP = 4, PV_FAIL = 8 };
 // reciprocal; tan theta = sign(1, cot 2theta) / (|cot 2theta| +
 // sqrt(1 + cot^2 2theta)) written on num/den without forming the cotangent:
 // sign(num) den / (|num| + hypot(num, den)).
+// T = double in the FP64 sweeps; T = float in the FP32 bulk sweeps, whose
+// inputs (dot products of FP32 columns) carry FP32 errors anyway.
 enum : int { RC_SKIP = 0, RC_ROT = 1, RC_EXC = 2, RC_FAIL = 3 };
-struct RealChainA {
-  double rt, c, s;
+template <class T>
+struct RealChainAT {
+  T rt, c, s;
   int mode;
 };
+using RealChainA = RealChainAT<double>;
 
-__device__ __forceinline__ RealChainA real_chain_a(double a11, double a22, double a12, double x, double tol) {
-  RealChainA r;
-  r.rt = 1.0; r.c = 1.0; r.s = 0.0;
-  // relative orthogonality (Sec. 2.1), |a12| < sqrt(a11) sqrt(a22) tol and
-  // |x| < tol, compared in squares (no FP64 square roots)
+// relative orthogonality (Sec. 2.1), |a12| < sqrt(a11) sqrt(a22) tol and
+// |x| < tol.  FP64: compared in squares (no FP64 square roots); FP32: with
+// square roots (cheap there), so that squares of small FP32 values cannot
+// underflow.
+__device__ __forceinline__ bool rel_orth(double a11, double a22, double a12, double x, double tol) {
   const double tol2 = tol * tol;
-  if (a12 * a12 < (a11 * a22) * tol2 && x * x < tol2) {
+  return a12 * a12 < (a11 * a22) * tol2 && x * x < tol2;
+}
+__device__ __forceinline__ bool rel_orth(float a11, float a22, float a12, float x, float tol) {
+  return fabsf(a12) < (sqrtf(a11) * sqrtf(a22)) * tol && fabsf(x) < tol;
+}
+
+template <class T>
+__device__ __forceinline__ RealChainAT<T> real_chain_a(T a11, T a22, T a12, T x, T tol) {
+  RealChainAT<T> r;
+  r.rt = T(1); r.c = T(1); r.s = T(0);
+  if (rel_orth(a11, a22, a12, x, tol)) {
     r.mode = RC_SKIP;
     return r;
   }
-  const double t2 = fma(-x, x, 1.0);
-  if (!(t2 > 0.0)) {
+  const T t2 = p_fma(-x, x, T(1));
+  if (!(t2 > T(0))) {
     r.mode = RC_FAIL;
     return r;
   }
-  r.rt = rsqrt(t2);
-  const double t = t2 * r.rt;
-  const double num = t * (a22 - a11);
-  const double den = 2.0 * a12 - (a11 + a22) * x;
-  if (num == 0.0 && den == 0.0) {
+  r.rt = p_rsqrt(t2);
+  const T t = t2 * r.rt;
+  const T num = t * (a22 - a11);
+  const T den = T(2) * a12 - (a11 + a22) * x;
+  if (num == T(0) && den == T(0)) {
     r.mode = RC_EXC;  // proportional pivots: cot 2theta = 0/0
     return r;
   }
-  const double hyp = sqrt(fma(num, num, den * den));
-  const double tn = sgn1(num) * den / (fabs(num) + hyp);
-  r.c = rsqrt(fma(tn, tn, 1.0));
+  const T hyp = p_sqrt(p_fma(num, num, den * den));
+  const T tn = sgn1(num) * den / (p_abs(num) + hyp);
+  r.c = p_rsqrt(p_fma(tn, tn, T(1)));
   r.s = tn * r.c;
   r.mode = RC_ROT;
   return r;
 }
 
-__device__ __forceinline__ void real_chain_b(double x, double& xi, double& eta) {
-  const double sp = sqrt(1.0 + x), sm = sqrt(1.0 - x);
-  const double q1 = sp + sm, q2 = (1.0 + sp) * (1.0 + sm);
-  const double rq = 1.0 / (q1 * q2);
+template <class T>
+__device__ __forceinline__ void real_chain_b(T x, T& xi, T& eta) {
+  const T sp = p_sqrt(T(1) + x), sm = p_sqrt(T(1) - x);
+  const T q1 = sp + sm, q2 = (T(1) + sp) * (T(1) + sm);
+  const T rq = T(1) / (q1 * q2);
   xi = x * q2 * rq;
   eta = x * q1 * rq;
 }
 
-__device__ __forceinline__ PivotOut real_combine(double a11, double a22, double a12, double x,
-                                                 const RealChainA& r, double xi, double eta, bool sort,
-                                                 bool f32cls, bool crit2) {
-  PivotOut o;
-  o.z12i = o.z21i = 0.0;
+template <class T>
+__device__ __forceinline__ PivotOutT<T> real_combine(T a11, T a22, T a12, T x, const RealChainAT<T>& r, T xi,
+                                                     T eta, bool sort, bool f32cls, bool crit2) {
+  PivotOutT<T> o;
+  o.z12i = o.z21i = T(0);
   o.flags = 0;
-  o.z11 = 1.0; o.z12 = 0.0; o.z21 = 0.0; o.z22 = 1.0;
+  o.z11 = T(1); o.z12 = T(0); o.z21 = T(0); o.z22 = T(1);
   if (r.mode == RC_SKIP) {
     if (sort && a11 < a22) o.flags |= PV_SWAP;
     return o;
@@ -164,19 +198,19 @@ __device__ __forceinline__ PivotOut real_combine(double a11, double a22, double 
     o.flags = PV_FAIL;
     return o;
   }
-  double cphi, cpsi;
+  T cphi, cpsi;
   if (r.mode == RC_EXC) {
     // signed form of the exception (reading of Sec. 2.1.2)
-    const double s = sgn1(x), ax = fabs(x);
-    const double p = rsqrt(2.0 * (1.0 + ax)), q = rsqrt(2.0 * (1.0 - ax));
+    const T s = sgn1(x), ax = p_abs(x);
+    const T p = p_rsqrt(T(2) * (T(1) + ax)), q = p_rsqrt(T(2) * (T(1) - ax));
     o.z11 = p; o.z12 = -s * q; o.z21 = s * p; o.z22 = q;
     cphi = o.z11; cpsi = o.z22;  // no t in this form
   } else {
-    const double c = r.c, s = r.s;
+    const T c = r.c, s = r.s;
     cphi = c + xi * (s - eta * c);
     cpsi = c - xi * (s + eta * c);
-    const double sphi = s - xi * (c + eta * s);
-    const double spsi = s + xi * (c - eta * s);
+    const T sphi = s - xi * (c + eta * s);
+    const T spsi = s + xi * (c - eta * s);
     o.z11 = cphi * r.rt;
     o.z12 = sphi * r.rt;
     o.z21 = -spsi * r.rt;
@@ -185,16 +219,14 @@ __device__ __forceinline__ PivotOut real_combine(double a11, double a22, double 
   o.flags = PV_ROT;
   bool small;
   if (crit2 && r.mode == RC_ROT)
-    small = f32cls ? (__double2float_rn(cphi) == 1.0f && __double2float_rn(cpsi) == 1.0f)
-                   : (cphi == 1.0 && cpsi == 1.0);
+    small = f32cls ? (f32_is_one(cphi) && f32_is_one(cpsi)) : (cphi == T(1) && cpsi == T(1));
   else
-    small = f32cls ? (__double2float_rn(o.z11) == 1.0f && __double2float_rn(o.z22) == 1.0f)
-                   : (o.z11 == 1.0 && o.z22 == 1.0);
+    small = f32cls ? (f32_is_one(o.z11) && f32_is_one(o.z22)) : (o.z11 == T(1) && o.z22 == T(1));
   if (!small) o.flags |= PV_BIG;
   if (sort) {
     // transformed diagonal of A-hat (Sec. 3.5.3, real case)
-    const double d1 = o.z11 * o.z11 * a11 + 2.0 * o.z11 * o.z21 * a12 + o.z21 * o.z21 * a22;
-    const double d2 = o.z12 * o.z12 * a11 + 2.0 * o.z22 * o.z12 * a12 + o.z22 * o.z22 * a22;
+    const T d1 = o.z11 * o.z11 * a11 + T(2) * o.z11 * o.z21 * a12 + o.z21 * o.z21 * a22;
+    const T d2 = o.z12 * o.z12 * a11 + T(2) * o.z22 * o.z12 * a12 + o.z22 * o.z22 * a22;
     if (d1 < d2) o.flags |= PV_SWAP;
   }
   return o;
@@ -202,10 +234,11 @@ __device__ __forceinline__ PivotOut real_combine(double a11, double a22, double 
 
 // Real pivot on one thread (both chains in sequence); the same arithmetic as
 // the two-warp form, so both give identical bits.
-__device__ __forceinline__ PivotOut pivot_real(double a11, double a22, double a12, double x, double tol,
-                                               bool sort, bool f32cls, bool crit2) {
-  const RealChainA r = real_chain_a(a11, a22, a12, x, tol);
-  double xi = 0.0, eta = 0.0;
+template <class T>
+__device__ __forceinline__ PivotOutT<T> pivot_real(T a11, T a22, T a12, T x, T tol, bool sort, bool f32cls,
+                                                   bool crit2) {
+  const RealChainAT<T> r = real_chain_a(a11, a22, a12, x, tol);
+  T xi = T(0), eta = T(0);
   if (r.mode == RC_ROT) real_chain_b(x, xi, eta);
   return real_combine(a11, a22, a12, x, r, xi, eta, sort, f32cls, crit2);
 }
@@ -214,68 +247,74 @@ __device__ __forceinline__ PivotOut pivot_real(double a11, double a22, double a1
 __device__ __forceinline__ void param_pair_barrier() { asm volatile("bar.sync 1, 64;\n" ::: "memory"); }
 
 // Complex pivot, Sec. 2.1.1.  a12 = (ar, ai), b12 = (br, bi).
-__device__ __forceinline__ PivotOut pivot_cplx(double a11, double a22, double ar, double ai,
-                                               double br, double bi, double tol, bool sort,
-                                               bool f32cls, bool crit2) {
-  PivotOut o;
-  o.flags = 0;
-  // relative orthogonality in squares: |a12|^2 < a11 a22 tol^2, |b12|^2 < tol^2
+__device__ __forceinline__ bool rel_orth_c(double a11, double a22, double absa2, double x2, double tol) {
   const double tol2 = tol * tol;
-  const double absa2 = fma(ar, ar, ai * ai);
-  const double x2 = fma(br, br, bi * bi);
-  if (absa2 < (a11 * a22) * tol2 && x2 < tol2) {
-    o.z11 = 1.0; o.z12 = 0.0; o.z21 = 0.0; o.z22 = 1.0; o.z12i = 0.0; o.z21i = 0.0;
+  return absa2 < (a11 * a22) * tol2 && x2 < tol2;
+}
+__device__ __forceinline__ bool rel_orth_c(float a11, float a22, float absa2, float x2, float tol) {
+  return sqrtf(absa2) < (sqrtf(a11) * sqrtf(a22)) * tol && sqrtf(x2) < tol;
+}
+
+template <class T>
+__device__ __forceinline__ PivotOutT<T> pivot_cplx(T a11, T a22, T ar, T ai, T br, T bi, T tol, bool sort,
+                                                   bool f32cls, bool crit2) {
+  PivotOutT<T> o;
+  o.flags = 0;
+  // relative orthogonality: |a12|^2 < a11 a22 tol^2, |b12|^2 < tol^2
+  const T absa2 = p_fma(ar, ar, ai * ai);
+  const T x2 = p_fma(br, br, bi * bi);
+  if (rel_orth_c(a11, a22, absa2, x2, tol)) {
+    o.z11 = T(1); o.z12 = T(0); o.z21 = T(0); o.z22 = T(1); o.z12i = T(0); o.z21i = T(0);
     if (sort && a11 < a22) o.flags |= PV_SWAP;
     return o;
   }
-  const double x = hypot(br, bi);
-  const double t2 = fma(-x, x, 1.0);
-  if (!(t2 > 0.0)) {
-    o.z11 = 1.0; o.z12 = 0.0; o.z21 = 0.0; o.z22 = 1.0; o.z12i = 0.0; o.z21i = 0.0;
+  const T x = p_hypot(br, bi);
+  const T t2 = p_fma(-x, x, T(1));
+  if (!(t2 > T(0))) {
+    o.z11 = T(1); o.z12 = T(0); o.z21 = T(0); o.z22 = T(1); o.z12i = T(0); o.z21i = T(0);
     o.flags = PV_FAIL;
     return o;
   }
-  const double rt = rsqrt(t2);
-  const double t = t2 * rt;
+  const T rt = p_rsqrt(t2);
+  const T t = t2 * rt;
   // e^{i zeta} = b12 / |b12| (1 if b12 = 0); z = e^{-i zeta} a12
-  double er = 1.0, ei = 0.0;
-  if (x != 0.0) {
-    const double rx = 1.0 / x;
+  T er = T(1), ei = T(0);
+  if (x != T(0)) {
+    const T rx = T(1) / x;
     er = br * rx;
     ei = bi * rx;
   }
-  const double u = er * ar + ei * ai;
-  const double v = er * ai - ei * ar;
-  const double h = a22 - a11;
-  double cphi, cpsi;
-  if (v == 0.0 && h == 0.0) {
-    const double p = rsqrt(2.0 * (1.0 + x)), q = rsqrt(2.0 * (1.0 - x));
+  const T u = er * ar + ei * ai;
+  const T v = er * ai - ei * ar;
+  const T h = a22 - a11;
+  T cphi, cpsi;
+  if (v == T(0) && h == T(0)) {
+    const T p = p_rsqrt(T(2) * (T(1) + x)), q = p_rsqrt(T(2) * (T(1) - x));
     o.z11 = p; o.z22 = q;
     o.z12 = -er * q; o.z12i = -ei * q;   // -e^{i zeta} q
     o.z21 = er * p;  o.z21i = -ei * p;   //  e^{-i zeta} p
     cphi = o.z11; cpsi = o.z22;
     o.flags = PV_ROT;
-    const bool small = f32cls ? (__double2float_rn(o.z11) == 1.0f && __double2float_rn(o.z22) == 1.0f)
-                              : (o.z11 == 1.0 && o.z22 == 1.0);
+    const bool small = f32cls ? (f32_is_one(o.z11) && f32_is_one(o.z22)) : (o.z11 == T(1) && o.z22 == T(1));
     if (!small) o.flags |= PV_BIG;
   } else {
-    const double tau = sgn1(h);
-    const double tan2 = tau * (2.0 * u - (a11 + a22) * x) / (t * sqrt(fma(h, h, 4.0 * v * v)));
-    const double tang = 2.0 * v / h;
-    double c2, s2, cg, sg;
+    const T tau = sgn1(h);
+    const T tan2 = tau * (T(2) * u - (a11 + a22) * x) / (t * p_sqrt(p_fma(h, h, T(4) * v * v)));
+    const T tang = T(2) * v / h;
+    T c2, s2, cg, sg;
     trig_from_tan(tan2, c2, s2);
     trig_from_tan(tang, cg, sg);
-    const double tcc = t * cg * c2;
-    cphi = sqrt(0.5 * (1.0 + x * s2 + tcc));
-    cpsi = sqrt(0.5 * (1.0 - x * s2 + tcc));
-    const double w = t * sg * c2;
+    const T tcc = t * cg * c2;
+    cphi = p_sqrt(T(0.5) * (T(1) + x * s2 + tcc));
+    cpsi = p_sqrt(T(0.5) * (T(1) - x * s2 + tcc));
+    const T w = t * sg * c2;
     // 1/(2 cos psi) and 1/(2 cos phi) from one reciprocal
-    const double r4 = 1.0 / (4.0 * cphi * cpsi);
-    const double ipsi = 2.0 * cphi * r4, iphi = 2.0 * cpsi * r4;
+    const T r4 = T(1) / (T(4) * cphi * cpsi);
+    const T ipsi = T(2) * cphi * r4, iphi = T(2) * cpsi * r4;
     // e^{i alpha} sin(phi) = e^{i zeta} ((s2 - x) + i w) / (2 cos psi)
-    const double pa = (s2 - x) * ipsi, qa = w * ipsi;
+    const T pa = (s2 - x) * ipsi, qa = w * ipsi;
     // e^{-i beta} sin(psi) = e^{-i zeta} ((s2 + x) - i w) / (2 cos phi)
-    const double pb = (s2 + x) * iphi, qb = -w * iphi;
+    const T pb = (s2 + x) * iphi, qb = -w * iphi;
     o.z11 = cphi * rt;
     o.z22 = cpsi * rt;
     o.z12 = (er * pa - ei * qa) * rt;
@@ -286,19 +325,17 @@ __device__ __forceinline__ PivotOut pivot_cplx(double a11, double a22, double ar
     o.flags = PV_ROT;
     bool small;
     if (crit2)
-      small = f32cls ? (__double2float_rn(cphi) == 1.0f && __double2float_rn(cpsi) == 1.0f)
-                     : (cphi == 1.0 && cpsi == 1.0);
+      small = f32cls ? (f32_is_one(cphi) && f32_is_one(cpsi)) : (cphi == T(1) && cpsi == T(1));
     else
-      small = f32cls ? (__double2float_rn(o.z11) == 1.0f && __double2float_rn(o.z22) == 1.0f)
-                     : (o.z11 == 1.0 && o.z22 == 1.0);
+      small = f32cls ? (f32_is_one(o.z11) && f32_is_one(o.z22)) : (o.z11 == T(1) && o.z22 == T(1));
     if (!small) o.flags |= PV_BIG;
   }
   if (sort) {
     // transformed diagonal of A-hat: (Z^* A Z)_11 and _22, Z11 and Z22 real
-    const double re21a = o.z21 * ar - o.z21i * ai;          // Re(a12 * z21)
-    const double d1 = o.z11 * o.z11 * a11 + 2.0 * o.z11 * re21a + (o.z21 * o.z21 + o.z21i * o.z21i) * a22;
-    const double re12a = o.z12 * ar + o.z12i * ai;          // Re(conj(z12) * a12)
-    const double d2 = (o.z12 * o.z12 + o.z12i * o.z12i) * a11 + 2.0 * o.z22 * re12a + o.z22 * o.z22 * a22;
+    const T re21a = o.z21 * ar - o.z21i * ai;          // Re(a12 * z21)
+    const T d1 = o.z11 * o.z11 * a11 + T(2) * o.z11 * re21a + (o.z21 * o.z21 + o.z21i * o.z21i) * a22;
+    const T re12a = o.z12 * ar + o.z12i * ai;          // Re(conj(z12) * a12)
+    const T d2 = (o.z12 * o.z12 + o.z12i * o.z12i) * a11 + T(2) * o.z22 * re12a + o.z22 * o.z22 * a22;
     if (d1 < d2) o.flags |= PV_SWAP;
   }
   return o;

@@ -79,6 +79,7 @@ struct InnerParams {
   bool f32cls;         // classify small/big at FP32 resolution
   bool crit2;
   bool chol_skip;      // Cholesky failure: skip the visit (FP32 bulk) instead of failing
+  bool par32;          // FP32 bulk sweeps: 2x2 parameters in FP32 (else FP64)
 };
 
 int blk_vmax(int w, bool cplx);  // real-view width V of the kernels for this w

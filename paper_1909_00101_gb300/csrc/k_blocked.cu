@@ -242,20 +242,36 @@ struct PivZ {
   int flags;
 };
 
+// Packed upper triangle (i <= j) of an order-n matrix, column by column:
+// u = j (j + 1) / 2 + i.  Unpacks u into (i, j).
+__device__ __forceinline__ void unpack_upper(int u, int& i, int& j) {
+  int jj = (int)((sqrtf(8.0f * (float)u + 1.0f) - 1.0f) * 0.5f);
+  while (jj * (jj + 1) / 2 > u) --jj;
+  while ((jj + 1) * (jj + 2) / 2 <= u) ++jj;
+  j = jj;
+  i = u - jj * (jj + 1) / 2;
+}
+
 // Ti: data type of the inner sweeps (double, or float in FP32 bulk sweeps);
-// To: type of the outer data (partials and Z-tilde).
-template <class Ti, class To, bool CPLX, int V>
+// To: type of the outer data (partials and Z-tilde).  P32 (FP32 bulk sweeps
+// only): the whole pivot-pair step in FP32 -- partial sums, Choleskys and
+// 2x2 parameters; its inputs are FP32 Gram partials, so FP32 arithmetic is as
+// accurate as they are.  Otherwise the sums and Choleskys are FP64.
+template <class Ti, class To, bool CPLX, int V, bool P32>
 __global__ void __launch_bounds__(512) k_inner(BlkDims d, BlkBuffers b, int step, InnerParams prm) {
   constexpr int E = CPLX ? 2 : 1;
   constexpr int BMAX = CPLX ? V / 2 : V;  // max columns of the pair
+  using Tc = typename std::conditional<P32, float, double>::type;  // sums and Choleskys
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* A = reinterpret_cast<double*>(smem_raw);        // E * BMAX * BMAX
-  double* Bm = A + E * BMAX * BMAX;                       // E * BMAX * BMAX
-  Ti* Zh = reinterpret_cast<Ti*>(Bm + E * BMAX * BMAX);   // E * BMAX * BMAX
+  double* Ad = reinterpret_cast<double*>(smem_raw);       // E * BMAX * BMAX
+  double* Bd = Ad + E * BMAX * BMAX;                      // E * BMAX * BMAX
+  Ti* Zh = reinterpret_cast<Ti*>(Bd + E * BMAX * BMAX);   // E * BMAX * BMAX
   PivInT<Ti>* pin = reinterpret_cast<PivInT<Ti>*>(Zh + E * BMAX * BMAX);
   PivZ<Ti>* pout = reinterpret_cast<PivZ<Ti>*>(pin + BMAX / 2 + 1);
+  Tc* A = reinterpret_cast<Tc*>(Ad);
+  Tc* Bm = reinterpret_cast<Tc*>(Bd);
   __shared__ int s_ctr[4];  // all, big, fail, any-change
-  __shared__ double s_inv;
+  __shared__ Tc s_inv[2];
   __shared__ int s_bad;
   __shared__ double s_xi[32], s_eta[32];  // chain B of the real parameters
   __shared__ unsigned char s_pair[63][32][2];  // inner round-robin table (M - 1 steps x M / 2 pairs)
@@ -274,21 +290,24 @@ __global__ void __launch_bounds__(512) k_inner(BlkDims d, BlkBuffers b, int step
   }
 
   // 1. fixed-order sum of the partials into A-hat and B-hat (column-major,
-  //    upper triangle, FP64), then the conjugate mirror.
-  for (int idx = threadIdx.x; idx < bb * bb; idx += blockDim.x) {
-    const int j = idx / bb, i = idx % bb;
-    if (i > j) continue;
-    for (int mat = 0; mat < 2; ++mat) {
+  //    both triangles): the upper-triangle entries of both matrices as one
+  //    packed list, so that every lane of a warp has an entry.
+  {
+    const int nup = bb * (bb + 1) / 2;
+    for (int t = threadIdx.x; t < 2 * nup; t += blockDim.x) {
+      const int mat = t >= nup ? 1 : 0;
+      int i, j;
+      unpack_upper(t - mat * nup, i, j);
       const int s0 = mat ? d.rf : 0, s1 = mat ? S : d.rf;
-      double* M = mat ? Bm : A;
-      double re = 0.0, im = 0.0;
+      Tc* M = mat ? Bm : A;
+      Tc re = Tc(0), im = Tc(0);
       for (int s = s0; s < s1; ++s) {
         const To* Q = P + (size_t)s * V * V;
         if constexpr (!CPLX) {
-          re += (double)Q[i * V + j];
+          re += (Tc)Q[i * V + j];
         } else {
-          re += (double)Q[i * V + j] + (double)Q[(bb + i) * V + bb + j];
-          im += (double)Q[i * V + bb + j] - (double)Q[j * V + bb + i];
+          re += (Tc)Q[i * V + j] + (Tc)Q[(bb + i) * V + bb + j];
+          im += (Tc)Q[i * V + bb + j] - (Tc)Q[j * V + bb + i];
         }
       }
       if constexpr (!CPLX) {
@@ -296,55 +315,65 @@ __global__ void __launch_bounds__(512) k_inner(BlkDims d, BlkBuffers b, int step
         M[i * BMAX + j] = re;
       } else {
         M[2 * (j * BMAX + i)] = re;
-        M[2 * (j * BMAX + i) + 1] = (i == j) ? 0.0 : im;
+        M[2 * (j * BMAX + i) + 1] = (i == j) ? Tc(0) : im;
         M[2 * (i * BMAX + j)] = re;
-        M[2 * (i * BMAX + j) + 1] = (i == j) ? 0.0 : -im;
+        M[2 * (i * BMAX + j) + 1] = (i == j) ? Tc(0) : -im;
       }
     }
   }
   __syncthreads();
 
-  // 2. Cholesky A-hat = R^* R (upper R), then B-hat, in FP64; strict lower
-  //    triangle zeroed.  A non-positive pivot fails the visit.
-  for (int mat = 0; mat < 2; ++mat) {
-    double* M = mat ? Bm : A;
-    for (int k = 0; k < bb; ++k) {
-      if (threadIdx.x == 0) {
-        const double dkk = M[E * (k * BMAX + k)];
-        if (!(dkk > 0.0) || !isfinite(dkk)) {
-          s_bad = 1;
-          s_inv = 0.0;
-        } else {
-          const double r = sqrt(dkk);
-          M[E * (k * BMAX + k)] = r;
-          s_inv = 1.0 / r;
-        }
+  // 2. Choleskys A-hat = R^* R and B-hat = R^* R (upper R) side by side: the
+  //    pivot of A on warp 0 and of B on warp 1 (two SM sub-partitions; the
+  //    pivot chain is the serial part), 1/sqrt from one rsqrt; the row
+  //    scaling and the trailing updates of both as packed lists.  A
+  //    non-positive pivot fails the visit.  Strict lower triangles are not
+  //    read afterwards (zeroed in step 3).
+  for (int k = 0; k < bb; ++k) {
+    if (threadIdx.x == 0 || threadIdx.x == 32) {
+      const int mat = threadIdx.x >> 5;
+      Tc* M = mat ? Bm : A;
+      const Tc dkk = M[E * (k * BMAX + k)];
+      if (!(dkk > Tc(0)) || !isfinite(dkk)) {
+        s_bad = 1;
+        s_inv[mat] = Tc(0);
+      } else {
+        const Tc inv = p_rsqrt(dkk);
+        M[E * (k * BMAX + k)] = dkk * inv;
+        s_inv[mat] = inv;
       }
-      __syncthreads();
-      if (s_bad) break;
-      const double inv = s_inv;
-      for (int j = k + 1 + threadIdx.x; j < bb; j += blockDim.x) {
-        M[E * (j * BMAX + k)] *= inv;
-        if constexpr (CPLX) M[E * (j * BMAX + k) + 1] *= inv;
-      }
-      __syncthreads();
-      const int rem = bb - k - 1;
-      for (int idx = threadIdx.x; idx < rem * rem; idx += blockDim.x) {
-        const int j = k + 1 + idx / rem, i = k + 1 + idx % rem;
-        if (i > j) continue;
-        if constexpr (!CPLX) {
-          M[j * BMAX + i] = fma(-M[i * BMAX + k], M[j * BMAX + k], M[j * BMAX + i]);
-        } else {
-          // M_ij -= conj(R_ki) R_kj
-          const double kir = M[2 * (i * BMAX + k)], kii = M[2 * (i * BMAX + k) + 1];
-          const double kjr = M[2 * (j * BMAX + k)], kji = M[2 * (j * BMAX + k) + 1];
-          M[2 * (j * BMAX + i)] -= kir * kjr + kii * kji;
-          M[2 * (j * BMAX + i) + 1] -= kir * kji - kii * kjr;
-        }
-      }
-      __syncthreads();
     }
+    __syncthreads();
     if (s_bad) break;
+    const int rem = bb - k - 1;
+    for (int t = threadIdx.x; t < 2 * rem; t += blockDim.x) {
+      const int mat = t >= rem ? 1 : 0;
+      const int j = k + 1 + t - mat * rem;
+      Tc* M = mat ? Bm : A;
+      const Tc inv = s_inv[mat];
+      M[E * (j * BMAX + k)] *= inv;
+      if constexpr (CPLX) M[E * (j * BMAX + k) + 1] *= inv;
+    }
+    __syncthreads();
+    const int nrem = rem * (rem + 1) / 2;
+    for (int t = threadIdx.x; t < 2 * nrem; t += blockDim.x) {
+      const int mat = t >= nrem ? 1 : 0;
+      int i, j;
+      unpack_upper(t - mat * nrem, i, j);
+      i += k + 1;
+      j += k + 1;
+      Tc* M = mat ? Bm : A;
+      if constexpr (!CPLX) {
+        M[j * BMAX + i] = p_fma(-M[i * BMAX + k], M[j * BMAX + k], M[j * BMAX + i]);
+      } else {
+        // M_ij -= conj(R_ki) R_kj
+        const Tc kir = M[2 * (i * BMAX + k)], kii = M[2 * (i * BMAX + k) + 1];
+        const Tc kjr = M[2 * (j * BMAX + k)], kji = M[2 * (j * BMAX + k) + 1];
+        M[2 * (j * BMAX + i)] -= kir * kjr + kii * kji;
+        M[2 * (j * BMAX + i) + 1] -= kir * kji - kii * kjr;
+      }
+    }
+    __syncthreads();
   }
   if (s_bad) {
     if (threadIdx.x == 0) {
@@ -356,17 +385,17 @@ __global__ void __launch_bounds__(512) k_inner(BlkDims d, BlkBuffers b, int step
 
   // 3. F-hat, G-hat (inner data type, in place), Z-hat = I
   {
-    double tmpA[E * BMAX * BMAX / 512 + 1], tmpB[E * BMAX * BMAX / 512 + 1];
+    Tc tmpA[E * BMAX * BMAX / 512 + 1], tmpB[E * BMAX * BMAX / 512 + 1];
     int cnt = 0;
     for (int idx = threadIdx.x; idx < E * bb * bb; idx += blockDim.x, ++cnt) {
       const int j = idx / (E * bb), i = (idx % (E * bb)) / E, part = idx % E;
       const bool low = i > j;
-      tmpA[cnt] = low ? 0.0 : A[E * (j * BMAX + i) + part];
-      tmpB[cnt] = low ? 0.0 : Bm[E * (j * BMAX + i) + part];
+      tmpA[cnt] = low ? Tc(0) : A[E * (j * BMAX + i) + part];
+      tmpB[cnt] = low ? Tc(0) : Bm[E * (j * BMAX + i) + part];
     }
     __syncthreads();
-    Ti* Fh = reinterpret_cast<Ti*>(A);
-    Ti* Gh = reinterpret_cast<Ti*>(Bm);
+    Ti* Fh = reinterpret_cast<Ti*>(Ad);
+    Ti* Gh = reinterpret_cast<Ti*>(Bd);
     cnt = 0;
     for (int idx = threadIdx.x; idx < E * bb * bb; idx += blockDim.x, ++cnt) {
       Fh[idx] = static_cast<Ti>(tmpA[cnt]);
@@ -375,8 +404,8 @@ __global__ void __launch_bounds__(512) k_inner(BlkDims d, BlkBuffers b, int step
     }
     __syncthreads();
   }
-  Ti* Fh = reinterpret_cast<Ti*>(A);  // bb x bb, ld bb (E scalars per element)
-  Ti* Gh = reinterpret_cast<Ti*>(Bm);
+  Ti* Fh = reinterpret_cast<Ti*>(Ad);  // bb x bb, ld bb (E scalars per element)
+  Ti* Gh = reinterpret_cast<Ti*>(Bd);
 
   // 4. inner prescale (variant 0): z_j = 1/||g-hat_j||
   for (int j = warp; j < bb; j += nwarps) {
@@ -448,10 +477,47 @@ __global__ void __launch_bounds__(512) k_inner(BlkDims d, BlkBuffers b, int step
         }
       }
       __syncthreads();
-      // FP64 parameters, one pair per lane (npairs <= 32); real pivots run
-      // their two independent chains on warps 0 and 1 (two SM sub-partitions),
-      // complex pivots on warp 0.  Counters are warp-aggregated.
-      if (warp <= 1) {
+      // 2x2 parameters, one pair per lane (npairs <= 32).  FP64: real pivots
+      // run their two independent chains on warps 0 and 1 (two SM
+      // sub-partitions), complex pivots on warp 0.  FP32 bulk sweeps with
+      // par32: the whole pivot in FP32 on warp 0.  Counters are
+      // warp-aggregated.
+      auto count_flags = [&](int fl) {
+        const unsigned rot = __ballot_sync(FULL, fl & PV_ROT), big = __ballot_sync(FULL, fl & PV_BIG);
+        const unsigned bad = __ballot_sync(FULL, fl & PV_FAIL), chg = __ballot_sync(FULL, fl & (PV_ROT | PV_SWAP));
+        if (lane == 0) {
+          s_ctr[0] += __popc(rot);
+          s_ctr[1] += __popc(big);
+          if (bad) s_ctr[2] = 1;
+          if (chg) s_ctr[3] = 1;
+        }
+      };
+      bool done32 = false;
+      if constexpr (P32) {
+        {
+          done32 = true;
+          if (warp == 0) {
+            const bool act = lane < npairs && s_pair[st][lane < npairs ? lane : 0][1] < bb;
+            int fl = 0;
+            if (act) {
+              const PivInT<Ti> p = pin[lane];
+              PivotOutT<float> o;
+              if constexpr (!CPLX)
+                o = pivot_real<float>(p.a11, p.a22, p.ar, p.br, (float)tol, false, true, prm.crit2);
+              else
+                o = pivot_cplx<float>(p.a11, p.a22, p.ar, p.ai, p.br, p.bi, (float)tol, prm.sort, true, prm.crit2);
+              PivZ<Ti> q;
+              q.z11 = o.z11; q.z12 = o.z12; q.z21 = o.z21; q.z22 = o.z22;
+              q.z12i = o.z12i; q.z21i = o.z21i;
+              q.flags = o.flags;
+              pout[lane] = q;
+              fl = o.flags;
+            }
+            count_flags(fl);
+          }
+        }
+      }
+      if (!done32 && warp <= 1) {
         const bool act = lane < npairs && s_pair[st][lane < npairs ? lane : 0][1] < bb;
         int fl = 0;
         PivotOut o;
@@ -499,14 +565,7 @@ __global__ void __launch_bounds__(512) k_inner(BlkDims d, BlkBuffers b, int step
             pout[lane] = q;
             fl = o.flags;
           }
-          const unsigned rot = __ballot_sync(FULL, fl & PV_ROT), big = __ballot_sync(FULL, fl & PV_BIG);
-          const unsigned bad = __ballot_sync(FULL, fl & PV_FAIL), chg = __ballot_sync(FULL, fl & (PV_ROT | PV_SWAP));
-          if (lane == 0) {
-            s_ctr[0] += __popc(rot);
-            s_ctr[1] += __popc(big);
-            if (bad) s_ctr[2] = 1;
-            if (chg) s_ctr[3] = 1;
-          }
+          count_flags(fl);
         }
       }
       __syncthreads();
@@ -791,7 +850,8 @@ cudaError_t apply_v(const BlkDims& d, const BlkBuffers& b, int step, cudaStream_
 template <class Ti, class To, bool CPLX, int V>
 cudaError_t inner_v(const BlkDims& d, const BlkBuffers& b, int step, const InnerParams& p, cudaStream_t s) {
   const size_t smem = inner_smem<Ti, CPLX, V>();
-  auto kern = k_inner<Ti, To, CPLX, V>;
+  constexpr bool can32 = std::is_same<Ti, float>::value;
+  auto kern = (can32 && p.par32) ? k_inner<Ti, To, CPLX, V, can32> : k_inner<Ti, To, CPLX, V, false>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   kern<<<d.nslots, 512, smem, s>>>(d, b, step, p);

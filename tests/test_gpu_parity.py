@@ -193,6 +193,19 @@ def test_mixed_precision(hz, cplx):
     check(p.F, p.G, r, label="mixed cplx=%s" % cplx)
 
 
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("fp32_params", [0, 1])
+def test_mixed_fp32_parameters(hz, cplx, fp32_params):
+    """FP32 bulk sweeps with the pivot-pair step in FP32 (1, default) or FP64
+    (0); the FP64 sweeps that follow bring the result to the FP64 tolerance
+    all the same."""
+    p = make_pair(200, 160, 128, lo=1e-3, hi=1e3, cond=1e2, cplx=cplx, seed=22)
+    r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", block_w=16 if not cplx else 8, precision="mixed",
+                 fp32_params=fp32_params, shorten=0)
+    assert r.info["sweeps_fp32"] >= 1
+    check(p.F, p.G, r, label="mixed fp32_params=%d cplx=%s" % (fp32_params, cplx))
+
+
 # ------------------------------------------------------- reproducibility ----
 
 @pytest.mark.parametrize("kw", [dict(path="pointwise"), dict(path="blocked", block_w=16),
