@@ -98,7 +98,7 @@ struct Plan {
   int mf, mg, n;
   int path;  // GSVD_PATH_POINTWISE / BLOCKED
   // blocked
-  int w = 0, nblk = 0, neff = 0, nslots = 0, steps = 0, rf = 1, rg = 1, V = 0;
+  int w = 0, nblk = 0, neff = 0, nslots = 0, steps = 0, rf = 1, rg = 1, rf32 = 1, rg32 = 1, V = 0;
   // workspace layout (bytes)
   size_t off_partial = 0, off_ztil = 0, off_flags = 0, off_ctr = 0, off_zdiag = 0, off_norms = 0,
          off_rank = 0, off_status = 0, off_work = 0, off_f32 = 0, off_g32 = 0, off_z32 = 0, off_table = 0,
@@ -157,21 +157,26 @@ bool make_plan(const gsvd_config& cfg, int dtype, int64_t mf, int64_t mg, int64_
   P.neff = P.nblk + (P.nblk & 1);
   P.nslots = P.neff / 2;
   P.steps = P.neff - 1;
-  // row splits of the Gram: about twelve CTAs per SM in total (so the uneven
-  // last wave costs little), whole 64-row tiles per split, no empty split
-  {
-    const int target = 12 * 152;
+  // row splits of the Gram, whole 64-row tiles per split, no empty split.
+  // FP64 (DMMA, pipe-bound): about twelve CTAs per SM in total, so the uneven
+  // last wave costs little.  FP32 (latency-bound, short CTAs): about four per
+  // SM, so that each CTA streams several tiles and the pivot kernel sums
+  // fewer partials.
+  auto splits = [&](int per_sm, int& rf, int& rg) {
+    const int target = per_sm * 152;
     const int s = std::max(2, (target + P.nslots - 1) / P.nslots);
     const int tf = (int)((mf + 63) / 64), tg = (int)((mg + 63) / 64);
     const int sf = std::max(1, (int)std::lround((double)s * tf / (double)(tf + tg)));
     const int sg = std::max(1, s - sf);
     const int pf = (tf + sf - 1) / sf, pg = (tg + sg - 1) / sg;  // tiles per split
-    P.rf = (tf + pf - 1) / pf;
-    P.rg = (tg + pg - 1) / pg;
-  }
+    rf = (tf + pf - 1) / pf;
+    rg = (tg + pg - 1) / pg;
+  };
+  splits(12, P.rf, P.rg);
+  splits(4, P.rf32, P.rg32);
   const size_t V2 = (size_t)P.V * P.V;
   size_t o = 0;
-  P.off_partial = o; o = align256(o + (size_t)P.nslots * (P.rf + P.rg) * V2 * 8);
+  P.off_partial = o; o = align256(o + (size_t)P.nslots * std::max(P.rf + P.rg, P.rf32 + P.rg32) * V2 * 8);
   P.off_ztil = o; o = align256(o + (size_t)P.nslots * V2 * 8);
   P.off_flags = o; o = align256(o + (size_t)P.nslots * 4);
   P.off_ctr = o; o = align256(o + NCTR * 8);
@@ -279,7 +284,9 @@ int run_sweeps(const Plan& P, const gsvd_config& cfg, bool fp32, void* F, long l
                gsvd_info* info) {
   BlkDims d;
   d.mf = P.mf; d.mg = P.mg; d.n = P.n; d.w = P.w; d.nblk = P.nblk; d.nslots = P.nslots;
-  d.rf = P.rf; d.rg = P.rg; d.trows = 64;
+  d.rf = fp32 ? P.rf32 : P.rf;
+  d.rg = fp32 ? P.rg32 : P.rg;
+  d.trows = 64;
   BlkBuffers b;
   b.F = F; b.ldf = ldf; b.G = G; b.ldg = ldg; b.Z = Z; b.ldz = ldz;
   b.partial = ws + P.off_partial;

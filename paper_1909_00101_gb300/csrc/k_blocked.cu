@@ -220,10 +220,13 @@ __global__ void __launch_bounds__(gram_threads<T, V>()) k_gram(BlkDims d, BlkBuf
       }
       __syncthreads();
     }
+    // the real Gram is symmetric and acc[u][v] (entry (tx + 16u, ty + 16v))
+    // has the same bits as its mirror, so it is stored as entry
+    // (ty + 16v, tx + 16u): consecutive lanes write consecutive addresses
 #pragma unroll
     for (int u = 0; u < NV; ++u)
 #pragma unroll
-      for (int v = 0; v < NV; ++v) out[(tx + 16 * u) * V + ty + 16 * v] = acc[u][v];
+      for (int v = 0; v < NV; ++v) out[(ty + 16 * v) * V + tx + 16 * u] = acc[u][v];
   }
 }
 
@@ -268,6 +271,7 @@ __global__ void __launch_bounds__(512) k_inner(BlkDims d, BlkBuffers b, int step
   Ti* Zh = reinterpret_cast<Ti*>(Bd + E * BMAX * BMAX);   // E * BMAX * BMAX
   PivInT<Ti>* pin = reinterpret_cast<PivInT<Ti>*>(Zh + E * BMAX * BMAX);
   PivZ<Ti>* pout = reinterpret_cast<PivZ<Ti>*>(pin + BMAX / 2 + 1);
+  uint16_t* s_tri = reinterpret_cast<uint16_t*>(pout + BMAX / 2 + 1);  // BMAX (BMAX + 1) / 2
   Tc* A = reinterpret_cast<Tc*>(Ad);
   Tc* Bm = reinterpret_cast<Tc*>(Bd);
   __shared__ int s_ctr[4];  // all, big, fail, any-change
@@ -289,46 +293,97 @@ __global__ void __launch_bounds__(512) k_inner(BlkDims d, BlkBuffers b, int step
     atomicAdd(&b.ctr[4], 1ull);
   }
 
+  // packed upper triangle (i <= j) of the pair's order, column by column:
+  // entry u = j (j + 1) / 2 + i holds i | j << 8.  Its first r (r + 1) / 2
+  // entries are the packed triangle of order r, for every r <= bb.
+  const int nup = bb * (bb + 1) / 2;
+  for (int u = threadIdx.x; u < nup; u += blockDim.x) {
+    int i, j;
+    unpack_upper(u, i, j);
+    s_tri[u] = (uint16_t)(i | (j << 8));
+  }
+  __syncthreads();
+
   // 1. fixed-order sum of the partials into A-hat and B-hat (column-major,
   //    both triangles): the upper-triangle entries of both matrices as one
-  //    packed list, so that every lane of a warp has an entry.
-  {
-    const int nup = bb * (bb + 1) / 2;
-    for (int t = threadIdx.x; t < 2 * nup; t += blockDim.x) {
-      const int mat = t >= nup ? 1 : 0;
-      int i, j;
-      unpack_upper(t - mat * nup, i, j);
-      const int s0 = mat ? d.rf : 0, s1 = mat ? S : d.rf;
-      Tc* M = mat ? Bm : A;
-      Tc re = Tc(0), im = Tc(0);
-      for (int s = s0; s < s1; ++s) {
-        const To* Q = P + (size_t)s * V * V;
-        if constexpr (!CPLX) {
-          re += (Tc)Q[i * V + j];
-        } else {
-          re += (Tc)Q[i * V + j] + (Tc)Q[(bb + i) * V + bb + j];
-          im += (Tc)Q[i * V + bb + j] - (Tc)Q[j * V + bb + i];
-        }
-      }
+  //    packed list, so that every lane of a warp has an entry; the loads of
+  //    eight partials are issued before their (sequential) sum.  Entries go
+  //    row by row (i fixed, j rising along the lanes) so that a warp reads
+  //    consecutive addresses of each partial: row-major entry u is the
+  //    column-major entry nup - 1 - u of the flipped index pair.
+  for (int t = threadIdx.x; t < 2 * nup; t += blockDim.x) {
+    const int mat = t >= nup ? 1 : 0;
+    const int ij = s_tri[nup - 1 - (t - mat * nup)];
+    const int i = bb - 1 - (ij >> 8), j = bb - 1 - (ij & 255);
+    const int s0 = mat ? d.rf : 0, s1 = mat ? S : d.rf;
+    Tc* M = mat ? Bm : A;
+    Tc re = Tc(0), im = Tc(0);
+#pragma unroll 8
+    for (int s = s0; s < s1; ++s) {
+      const To* Q = P + (size_t)s * V * V;
       if constexpr (!CPLX) {
-        M[j * BMAX + i] = re;
-        M[i * BMAX + j] = re;
+        re += (Tc)Q[i * V + j];
       } else {
-        M[2 * (j * BMAX + i)] = re;
-        M[2 * (j * BMAX + i) + 1] = (i == j) ? Tc(0) : im;
-        M[2 * (i * BMAX + j)] = re;
-        M[2 * (i * BMAX + j) + 1] = (i == j) ? Tc(0) : -im;
+        re += (Tc)Q[i * V + j] + (Tc)Q[(bb + i) * V + bb + j];
+        im += (Tc)Q[i * V + bb + j] - (Tc)Q[j * V + bb + i];
       }
+    }
+    if constexpr (!CPLX) {
+      M[j * BMAX + i] = re;
+      M[i * BMAX + j] = re;
+    } else {
+      M[2 * (j * BMAX + i)] = re;
+      M[2 * (j * BMAX + i) + 1] = (i == j) ? Tc(0) : im;
+      M[2 * (i * BMAX + j)] = re;
+      M[2 * (i * BMAX + j) + 1] = (i == j) ? Tc(0) : -im;
     }
   }
   __syncthreads();
 
   // 2. Choleskys A-hat = R^* R and B-hat = R^* R (upper R) side by side: the
   //    pivot of A on warp 0 and of B on warp 1 (two SM sub-partitions; the
-  //    pivot chain is the serial part), 1/sqrt from one rsqrt; the row
-  //    scaling and the trailing updates of both as packed lists.  A
-  //    non-positive pivot fails the visit.  Strict lower triangles are not
-  //    read afterwards (zeroed in step 3).
+  //    pivot chain is the serial part), 1/sqrt from one rsqrt; the trailing
+  //    updates of both as packed lists.  FP64: the row k of R is scaled in
+  //    its own pass before the update (one FP64 multiply per entry); FP32:
+  //    the update scales the two row entries it reads and the row itself is
+  //    scaled while the next pivot is taken (same products, one barrier
+  //    less).  A non-positive pivot fails the visit.  Strict lower
+  //    triangles are not read afterwards (zeroed in step 3).
+  auto update = [&](int k, bool scaled) {
+    const int rem = bb - k - 1;
+    const int nrem = rem * (rem + 1) / 2;
+    for (int t = threadIdx.x; t < 2 * nrem; t += blockDim.x) {
+      const int mat = t >= nrem ? 1 : 0;
+      const int ij = s_tri[t - mat * nrem];
+      const int i = k + 1 + (ij & 255), j = k + 1 + (ij >> 8);
+      Tc* M = mat ? Bm : A;
+      const Tc sc = scaled ? Tc(1) : s_inv[mat];
+      if constexpr (!CPLX) {
+        Tc rki = M[i * BMAX + k], rkj = M[j * BMAX + k];
+        if (!scaled) { rki *= sc; rkj *= sc; }
+        M[j * BMAX + i] = p_fma(-rki, rkj, M[j * BMAX + i]);
+      } else {
+        // M_ij -= conj(R_ki) R_kj
+        Tc kir = M[2 * (i * BMAX + k)], kii = M[2 * (i * BMAX + k) + 1];
+        Tc kjr = M[2 * (j * BMAX + k)], kji = M[2 * (j * BMAX + k) + 1];
+        if (!scaled) { kir *= sc; kii *= sc; kjr *= sc; kji *= sc; }
+        M[2 * (j * BMAX + i)] -= kir * kjr + kii * kji;
+        M[2 * (j * BMAX + i) + 1] -= kir * kji - kii * kjr;
+      }
+    }
+  };
+  auto scale_row = [&](int k, Tc inv0, Tc inv1) {
+    const int rem = bb - k - 1;
+    for (int t = threadIdx.x; t < 2 * rem; t += blockDim.x) {
+      const int mat = t >= rem ? 1 : 0;
+      const int j = k + 1 + t - mat * rem;
+      Tc* M = mat ? Bm : A;
+      const Tc inv = mat ? inv1 : inv0;
+      M[E * (j * BMAX + k)] *= inv;
+      if constexpr (CPLX) M[E * (j * BMAX + k) + 1] *= inv;
+    }
+  };
+  Tc prev0 = Tc(0), prev1 = Tc(0);  // FP32: pivots of the row still to scale
   for (int k = 0; k < bb; ++k) {
     if (threadIdx.x == 0 || threadIdx.x == 32) {
       const int mat = threadIdx.x >> 5;
@@ -343,35 +398,20 @@ __global__ void __launch_bounds__(512) k_inner(BlkDims d, BlkBuffers b, int step
         s_inv[mat] = inv;
       }
     }
-    __syncthreads();
-    if (s_bad) break;
-    const int rem = bb - k - 1;
-    for (int t = threadIdx.x; t < 2 * rem; t += blockDim.x) {
-      const int mat = t >= rem ? 1 : 0;
-      const int j = k + 1 + t - mat * rem;
-      Tc* M = mat ? Bm : A;
-      const Tc inv = s_inv[mat];
-      M[E * (j * BMAX + k)] *= inv;
-      if constexpr (CPLX) M[E * (j * BMAX + k) + 1] *= inv;
+    if constexpr (P32) {
+      if (k > 0) scale_row(k - 1, prev0, prev1);  // row k-1: not read by pivot k
     }
     __syncthreads();
-    const int nrem = rem * (rem + 1) / 2;
-    for (int t = threadIdx.x; t < 2 * nrem; t += blockDim.x) {
-      const int mat = t >= nrem ? 1 : 0;
-      int i, j;
-      unpack_upper(t - mat * nrem, i, j);
-      i += k + 1;
-      j += k + 1;
-      Tc* M = mat ? Bm : A;
-      if constexpr (!CPLX) {
-        M[j * BMAX + i] = p_fma(-M[i * BMAX + k], M[j * BMAX + k], M[j * BMAX + i]);
-      } else {
-        // M_ij -= conj(R_ki) R_kj
-        const Tc kir = M[2 * (i * BMAX + k)], kii = M[2 * (i * BMAX + k) + 1];
-        const Tc kjr = M[2 * (j * BMAX + k)], kji = M[2 * (j * BMAX + k) + 1];
-        M[2 * (j * BMAX + i)] -= kir * kjr + kii * kji;
-        M[2 * (j * BMAX + i) + 1] -= kir * kji - kii * kjr;
-      }
+    if (s_bad) break;
+    if constexpr (P32) {
+      prev0 = s_inv[0];
+      prev1 = s_inv[1];
+      update(k, false);
+      if (k == bb - 1) scale_row(k, prev0, prev1);  // empty (no entries right of the last pivot)
+    } else {
+      scale_row(k, s_inv[0], s_inv[1]);
+      __syncthreads();
+      update(k, true);
     }
     __syncthreads();
   }
@@ -817,7 +857,8 @@ size_t inner_smem() {
   constexpr int E = CPLX ? 2 : 1;
   constexpr int BMAX = CPLX ? V / 2 : V;
   return sizeof(double) * 2 * E * BMAX * BMAX + sizeof(Ti) * E * BMAX * BMAX +
-         sizeof(PivInT<Ti>) * (BMAX / 2 + 1) + sizeof(PivZ<Ti>) * (BMAX / 2 + 1) + 16;
+         sizeof(PivInT<Ti>) * (BMAX / 2 + 1) + sizeof(PivZ<Ti>) * (BMAX / 2 + 1) +
+         sizeof(uint16_t) * (BMAX * (BMAX + 1) / 2) + 16;
 }
 
 template <class K>
@@ -897,6 +938,7 @@ cudaError_t launch_apply(const BlkDims& d, const BlkBuffers& b, bool cplx, bool 
     else { HZ_DISPATCH_V(V, (apply_v<double, false, VV>(d, b, step, s))); }
   }
 }
+
 
 cudaError_t launch_inner(const BlkDims& d, const BlkBuffers& b, bool cplx, bool fp32, int step,
                          const InnerParams& p, cudaStream_t s) {
