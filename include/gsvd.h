@@ -87,6 +87,10 @@ typedef struct {
   int32_t fp32_params;      /* mixed precision: 1 = the pivot-pair step of the FP32 bulk sweeps (partial
                                Gram sums, the two Choleskys, the 2x2 parameters) in FP32, whose inputs
                                are FP32 dot products anyway (default); 0 = those in FP64 */
+  int32_t fp64_gemm;        /* blocked FP64 sweeps: pivot Grams and block applies 1 = on the BF16 tensor
+                               cores with FP64 accuracy (operands split into 8-bit integer slices,
+                               exact level sums, one rounding; default, block widths with 2w <= 32
+                               real / 4w <= 32 complex), 0 = FP64 DMMA */
 } gsvd_config;
 
 /* One problem.  dtype = GSVD_R64 or GSVD_C128. */

@@ -12,8 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgsvd_gb300.so")
-SOURCES = ["gsvd_api.cu", "k_blocked.cu", "k_pointwise.cu", "k_columns.cu", "k_qr.cu", "gsvd_noalloc.cu"]
-HEADERS = ["hz_device.cuh", "hz_kernels.h"]
+SOURCES = ["gsvd_api.cu", "k_blocked.cu", "k_pointwise.cu", "k_columns.cu", "k_qr.cu", "k_ozaki.cu", "gsvd_noalloc.cu"]
+HEADERS = ["hz_device.cuh", "hz_kernels.h", "blk_pair.cuh"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-lineinfo",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall", "-cudart", "shared"]
 

@@ -1,5 +1,6 @@
 // fp_peaks.cu -- throughput probe of the arithmetic pipes this engine uses on
-// sm_103a: DFMA, DMMA (mma.sync m8n8k4 / m16n8k4 f64), FFMA, TF32 mma.sync, and
+// sm_103a: DFMA, DMMA (mma.sync m8n8k4 / m16n8k4 f64), FFMA, mma.sync with
+// TF32, BF16, FP16 (FP32 accumulation) and S8 (S32 accumulation) inputs, and
 // FP64 DFMA / sqrt / division with 1..32 active lanes per warp (does an FP64
 // warp instruction cost the same whatever the number of active lanes?).
 // Bounded loops only; prints one JSON object.
@@ -85,6 +86,49 @@ __global__ void k_tf32(float* out) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// mma.sync with 16-bit inputs (m16n8k16, FP32 accumulation): BF16 or FP16
+template <int IT, bool BF>
+__global__ void k_mma16(float* out) {
+  const unsigned a0 = 0x3c003c00u + threadIdx.x, b0 = 0x3c003c00u;
+  float c[4][4];
+  for (int j = 0; j < 4; j++)
+    for (int q = 0; q < 4; q++) c[j][q] = 0;
+  for (int i = 0; i < IT; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      if constexpr (BF)
+        asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+                     : "+f"(c[j][0]), "+f"(c[j][1]), "+f"(c[j][2]), "+f"(c[j][3])
+                     : "r"(a0), "r"(a0), "r"(a0), "r"(a0), "r"(b0), "r"(b0));
+      else
+        asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+                     : "+f"(c[j][0]), "+f"(c[j][1]), "+f"(c[j][2]), "+f"(c[j][3])
+                     : "r"(a0), "r"(a0), "r"(a0), "r"(a0), "r"(b0), "r"(b0));
+    }
+  float s = 0;
+  for (int j = 0; j < 4; j++)
+    for (int q = 0; q < 4; q++) s += c[j][q];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+// mma.sync with S8 inputs (m16n8k32, S32 accumulation)
+template <int IT>
+__global__ void k_mma_s8(int* out) {
+  const unsigned a0 = 0x01020304u + threadIdx.x, b0 = 0x01010101u;
+  int c[4][4];
+  for (int j = 0; j < 4; j++)
+    for (int q = 0; q < 4; q++) c[j][q] = 0;
+  for (int i = 0; i < IT; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+      asm volatile("mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+                   : "+r"(c[j][0]), "+r"(c[j][1]), "+r"(c[j][2]), "+r"(c[j][3])
+                   : "r"(a0), "r"(a0), "r"(a0), "r"(a0), "r"(b0), "r"(b0));
+  int s = 0;
+  for (int j = 0; j < 4; j++)
+    for (int q = 0; q < 4; q++) s += c[j][q];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 int main() {
   cudaDeviceProp p;
   CK(cudaGetDeviceProperties(&p, 0));
@@ -115,6 +159,12 @@ int main() {
   printf(", \"ffma_tflops\": %.3f", 2.0 * 16 * IT * 4 * warps * 32 / t / 1e9);
   t = time([&] { k_tf32<IT * 4><<<blocks, thr>>>((float*)d); });
   printf(", \"tf32_mma_sync_tflops\": %.2f", 2048.0 * 4 * (IT * 4) * warps / t / 1e9);
+  t = time([&] { k_mma16<IT * 4, true><<<blocks, thr>>>((float*)d); });
+  printf(", \"bf16_mma_sync_tflops\": %.2f", 4096.0 * 4 * (IT * 4) * warps / t / 1e9);
+  t = time([&] { k_mma16<IT * 4, false><<<blocks, thr>>>((float*)d); });
+  printf(", \"fp16_mma_sync_tflops\": %.2f", 4096.0 * 4 * (IT * 4) * warps / t / 1e9);
+  t = time([&] { k_mma_s8<IT * 4><<<blocks, thr>>>((int*)d); });
+  printf(", \"s8_mma_sync_tops\": %.2f", 8192.0 * 4 * (IT * 4) * warps / t / 1e9);
   printf(", \"fp64_by_active_lanes\": [");
   const int act[5] = {1, 4, 8, 16, 32};
   for (int r = 0; r < 5; r++) {

@@ -284,8 +284,11 @@ int run_sweeps(const Plan& P, const gsvd_config& cfg, bool fp32, void* F, long l
                gsvd_info* info) {
   BlkDims d;
   d.mf = P.mf; d.mg = P.mg; d.n = P.n; d.w = P.w; d.nblk = P.nblk; d.nslots = P.nslots;
-  d.rf = fp32 ? P.rf32 : P.rf;
-  d.rg = fp32 ? P.rg32 : P.rg;
+  // FP64 sweeps: Gram and apply on the tensor cores (sliced operands) or on
+  // the FP64 pipe (DMMA)
+  const bool oz = !fp32 && cfg.fp64_gemm == 1 && oz_supported(P.V);
+  d.rf = (fp32 || oz) ? P.rf32 : P.rf;
+  d.rg = (fp32 || oz) ? P.rg32 : P.rg;
   d.trows = 64;
   BlkBuffers b;
   b.F = F; b.ldf = ldf; b.G = G; b.ldg = ldg; b.Z = Z; b.ldz = ldz;
@@ -318,11 +321,11 @@ int run_sweeps(const Plan& P, const gsvd_config& cfg, bool fp32, void* F, long l
     CK(cudaMemsetAsync(b.ctr, 0, NCTR * sizeof(unsigned long long), s));
     for (int k = 0; k < P.steps; ++k) {
       if (prof) kt.mark(kb + 0, s);
-      CK(launch_gram(d, b, P.cplx, fp32, k, s));
+      CK(oz ? launch_gram_oz(d, b, P.cplx, k, s) : launch_gram(d, b, P.cplx, fp32, k, s));
       if (prof) { kt.mark(kb + 0, s); kt.mark(kb + 1, s); }
       CK(launch_inner(d, b, P.cplx, fp32, k, ip, s));
       if (prof) { kt.mark(kb + 1, s); kt.mark(kb + 2, s); }
-      CK(launch_apply(d, b, P.cplx, fp32, k, s));
+      CK(oz ? launch_apply_oz(d, b, P.cplx, k, s) : launch_apply(d, b, P.cplx, fp32, k, s));
       if (prof) kt.mark(kb + 2, s);
     }
     CK(cudaMemcpyAsync(h_ctr, b.ctr, NCTR * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
@@ -759,6 +762,7 @@ void gsvd_config_default(gsvd_config* c) {
   c->inner_max_sweeps_fp32 = 1;
   c->shorten = 1;
   c->fp32_params = 1;
+  c->fp64_gemm = 1;
 }
 
 int gsvd_create(gsvd_handle* h, const gsvd_config* cfg, void* stream) {

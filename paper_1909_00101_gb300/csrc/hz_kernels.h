@@ -89,6 +89,11 @@ cudaError_t launch_inner(const BlkDims& d, const BlkBuffers& b, bool cplx, bool 
                          const InnerParams& p, cudaStream_t s);
 cudaError_t launch_apply(const BlkDims& d, const BlkBuffers& b, bool cplx, bool fp32, int step,
                          cudaStream_t s);
+// FP64 Gram and apply on the BF16 tensor cores with FP64 accuracy (sliced
+// operands, exact level sums); real-view widths V = 16 and 32
+bool oz_supported(int V);
+cudaError_t launch_gram_oz(const BlkDims& d, const BlkBuffers& b, bool cplx, int step, cudaStream_t s);
+cudaError_t launch_apply_oz(const BlkDims& d, const BlkBuffers& b, bool cplx, int step, cudaStream_t s);
 
 // -------------------------------------------------- column operations ----
 // prescale: z_j = 1/||g_j||, F <- F Z0, G <- G Z0, Z <- Z0 (FP64, in place)

@@ -19,6 +19,7 @@
 // of blocks of W^T W, and Y Z = [Re Y, Im Y] [[Re Z, Im Z], [-Im Z, Re Z]].
 #include <type_traits>
 
+#include "blk_pair.cuh"
 #include "hz_device.cuh"
 #include "hz_kernels.h"
 
@@ -32,24 +33,6 @@ __device__ __forceinline__ void dmma884(double& c0, double& c1, double a, double
   asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
                : "+d"(c0), "+d"(c1)
                : "d"(a), "d"(b));
-}
-
-struct PairCols {
-  int cp, wp, cq, wq, bb;
-  __device__ __forceinline__ int gcol(int c) const { return c < wp ? cp + c : cq + (c - wp); }
-};
-
-__device__ __forceinline__ bool load_pair(const BlkDims& d, const BlkBuffers& b, int step, int slot,
-                                          PairCols& pc) {
-  const uint16_t* pr = b.table + ((size_t)step * d.nslots + slot) * 2;
-  const int p = pr[0], q = pr[1];
-  if (p >= d.nblk || q >= d.nblk) return false;
-  pc.cp = p * d.w;
-  pc.wp = min(d.w, d.n - pc.cp);
-  pc.cq = q * d.w;
-  pc.wq = min(d.w, d.n - pc.cq);
-  pc.bb = pc.wp + pc.wq;
-  return true;
 }
 
 // Load rows [r0, r0+TR) of the real view of [Y_p Y_q] (zero outside) into

@@ -2,8 +2,8 @@
 
     python -m paper_1909_00101_gb300.fp_peaks
 
-Prints one JSON object: DFMA, DMMA (FP64 mma.sync), FFMA and TF32 mma.sync
-throughput, and FP64 DFMA/sqrt/division time with 1, 4, 8, 16, 32 active
+Prints one JSON object: DFMA, DMMA (FP64 mma.sync), FFMA and mma.sync (TF32,
+BF16, FP16, S8 inputs) throughput, and FP64 DFMA/sqrt/division time with 1, 4, 8, 16, 32 active
 lanes per warp (equal times = cost per warp instruction, not per lane).
 """
 import os
