@@ -52,53 +52,93 @@ __device__ __forceinline__ int exp_field(double x) {
   return e ? e : 1;
 }
 
-// The seven signed 8-bit digits of x relative to the scale whose exponent
-// field is emax (|x| < 2^(emax - 1022)), as BF16 bit patterns; eadd is added
-// to x's exponent first (x 2^eadd is sliced; x != 0 assumed normal).
-__device__ __forceinline__ void slice7(double x, int emax, int eadd, uint16_t out[NSL]) {
+// The 56-bit fixed-point magnitude X of x relative to the scale whose
+// exponent field is emax (|x| < 2^(emax - 1022), X = |x| 2^(1078 - emax),
+// truncated); eadd is added to x's exponent first (x 2^eadd is taken).
+__device__ __forceinline__ unsigned long long fixed56(double x, int emax, int eadd) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   const int e = (int)((bits >> 52) & 0x7FF);
   const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull);
   const int sh = (e ? e + eadd : 1 + eadd) - emax + 3;
-  unsigned long long X = 0;
-  if (m != 0) {
-    if (sh >= 0)
-      X = m << sh;  // sh <= 3: X < 2^56
-    else if (sh > -64)
-      X = m >> (-sh);
-  }
-  const uint16_t sgn = (bits >> 63) ? 0x8000u : 0u;
-#pragma unroll
-  for (int a = 0; a < NSL; ++a) {
-    const unsigned c = (unsigned)(X >> (48 - 8 * a)) & 255u;
-    // an integer below 256 has at most 8 significant bits: its FP32 pattern's
-    // low 16 bits are zero and the high half is its BF16 pattern
-    out[a] = c ? (uint16_t)((__float_as_uint((float)c) >> 16) | sgn) : (uint16_t)0;
-  }
+  if (sh >= 0) return m << sh;  // sh <= 3: X < 2^56
+  return sh > -64 ? (m >> (-sh)) : 0ull;
 }
 
-// T 2^e2 rounded to the nearest FP64 value (ties to even); T 2^e2 is assumed
-// to be 0 or in the normal range.
-__device__ __forceinline__ double i128_to_double(__int128 T, int e2) {
-  if (T == 0) return 0.0;
-  const bool neg = T < 0;
-  unsigned __int128 U = neg ? (unsigned __int128)(-T) : (unsigned __int128)T;
-  const unsigned long long h = (unsigned long long)(U >> 64), l = (unsigned long long)U;
-  const int lz = h ? __clzll((long long)h) : 64 + __clzll((long long)l);
-  U <<= lz;
-  const unsigned long long top = (unsigned long long)(U >> 64), rest = (unsigned long long)U;
-  unsigned long long m = top >> 11;
-  const unsigned long long r = top & 0x7FFull;
-  const bool up = r > 0x400ull || (r == 0x400ull && (rest != 0 || (m & 1ull)));
-  m += up ? 1ull : 0ull;
-  int ex = 127 - lz + e2;
+// BF16 pattern of the integer c in [0, 255], with the sign bit sgn: the FP32
+// value 2^23 + c minus 2^23 is exactly c, and an integer below 256 has at
+// most 8 significant bits, so its FP32 pattern's high half is its BF16
+// pattern (c = 0 gives a signed zero, which adds nothing).
+__device__ __forceinline__ uint32_t bf16_digit(uint32_t c, uint32_t sgn) {
+  const float f = __uint_as_float(0x4B000000u | c) - 8388608.0f;
+  return (__float_as_uint(f) >> 16) | sgn;
+}
+
+// The seven signed 8-bit digits of x (most significant first) as BF16
+// patterns in the low halves of out[]: x = s 2^e sum_a c_a 2^(-8(a+1)) + r.
+__device__ __forceinline__ void slice7(double x, int emax, int eadd, uint32_t out[NSL]) {
+  const unsigned long long X = fixed56(x, emax, eadd);
+  const uint32_t sgn = (uint32_t)((unsigned long long)__double_as_longlong(x) >> 63) << 15;
+  const uint32_t h = (uint32_t)(X >> 32), l = (uint32_t)X;
+  out[0] = bf16_digit((h >> 16) & 255u, sgn);
+  out[1] = bf16_digit((h >> 8) & 255u, sgn);
+  out[2] = bf16_digit(h & 255u, sgn);
+  out[3] = bf16_digit(l >> 24, sgn);
+  out[4] = bf16_digit((l >> 16) & 255u, sgn);
+  out[5] = bf16_digit((l >> 8) & 255u, sgn);
+  out[6] = bf16_digit(l & 255u, sgn);
+}
+
+// An integer-valued FP32 value as a 64-bit integer, with integer operations
+// (the FP32 -> 64-bit conversion instruction would use the FP64 pipe).
+__device__ __forceinline__ long long float_int_to_ll(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const int e = (int)((b >> 23) & 255u);
+  if (e < 127) return 0;  // |f| < 1: an integer-valued f is 0
+  const long long m = (long long)((b & 0x7FFFFFu) | 0x800000u);
+  const long long v = e >= 150 ? (m << (e - 150)) : (m >> (150 - e));
+  return (b >> 31) ? -v : v;
+}
+
+// sum_i x_i 2^(8(6 - i)) 2^e2 rounded to the nearest FP64 value (ties to
+// even), with integer operations only.  The sum is formed exactly as
+// H 2^32 + L (H signed 64-bit, L unsigned 32-bit); |x_i| < 2^40 and a normal
+// (or zero) result are assumed.
+__device__ __forceinline__ double levels_to_double(const long long x[NLV], int e2) {
+  const long long hi = (x[0] << 16) + (x[1] << 8) + x[2];
+  const long long lo = (x[3] << 24) + (x[4] << 16) + (x[5] << 8) + x[6];
+  long long H = hi + (lo >> 32);
+  uint32_t L = (uint32_t)lo;
+  if (H == 0 && L == 0) return 0.0;
+  const bool neg = H < 0;
+  if (neg) {
+    H = -H - (L != 0 ? 1 : 0);
+    L = 0u - L;
+  }
+  unsigned long long W;
+  bool sticky;
+  int top;
+  if (H != 0) {
+    const int lz = __clzll(H);
+    const unsigned long long Lw = (unsigned long long)L << 32;
+    W = ((unsigned long long)H << lz) | (lz ? (Lw >> (64 - lz)) : 0ull);
+    sticky = (Lw << lz) != 0ull;
+    top = 95 - lz;
+  } else {
+    const int lz = __clzll((long long)(unsigned long long)L);
+    W = (unsigned long long)L << lz;
+    sticky = false;
+    top = 63 - lz;
+  }
+  unsigned long long m = W >> 11;
+  const uint32_t r = (uint32_t)W & 0x7FFu;
+  m += (r > 0x400u || (r == 0x400u && (sticky || (m & 1ull)))) ? 1ull : 0ull;
+  int ex = top + e2;
   if (m >> 53) {
     m >>= 1;
     ++ex;
   }
-  const unsigned long long out = (neg ? (1ull << 63) : 0ull) | ((unsigned long long)(ex + 1023) << 52) |
-                                 (m & 0xFFFFFFFFFFFFFull);
-  return __longlong_as_double((long long)out);
+  return __longlong_as_double((long long)((neg ? (1ull << 63) : 0ull) | ((unsigned long long)(ex + 1023) << 52) |
+                                          (m & 0xFFFFFFFFFFFFFull)));
 }
 
 __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2]) {
@@ -197,49 +237,58 @@ __global__ void __launch_bounds__(32 * oz_gram_warps<V>()) k_gram_oz(BlkDims d, 
     for (int q = 0; q < 4; ++q) hi[L][q] = lo[L][q] = 0.0f;
 
   // 2. chunks of 32 rows: slices of the real view into shared memory, then
-  //    the level products of this warp's tile, then the exact flush
-  for (int c0 = r0; c0 < r1; c0 += OZ_CHUNK) {
-    // row pairs (r, r + 1) of real-view column c; 16 pairs per column
-    for (int it = threadIdx.x; it < (V / E) * (OZ_CHUNK / 2); it += NT) {
-      const int c = it / (OZ_CHUNK / 2), rp = 2 * (it % (OZ_CHUNK / 2));
-      uint16_t s0[NSL], s1[NSL];
-      if constexpr (!CPLX) {
-        double x0 = 0.0, x1 = 0.0;
-        if (c < bb) {
-          const double* col = Y + (size_t)pc.gcol(c) * ld;
-          if (c0 + rp < r1) x0 = col[c0 + rp];
-          if (c0 + rp + 1 < r1) x1 = col[c0 + rp + 1];
-        }
-        const int em = s_emax[c];
-        slice7(x0, em, 0, s0);
-        slice7(x1, em, 0, s1);
+  //    the level products of this warp's tile, then the exact flush.  Item
+  //    it is the row pair (r, r + 1) of (real-view, or complex) column
+  //    it / 16; the next chunk's values are loaded while this one is used.
+  constexpr int ITEMS = (V / E) * (OZ_CHUNK / 2);
+  constexpr int PERT = (ITEMS + NT - 1) / NT;
+  double pre[PERT][2 * E];
+  auto fetch = [&](int c0) {
 #pragma unroll
-        for (int a = 0; a < NSL; ++a)
-          *reinterpret_cast<uint32_t*>(&Ss[a][c][rp]) = (uint32_t)s0[a] | ((uint32_t)s1[a] << 16);
-      } else {
+    for (int u = 0; u < PERT; ++u) {
+      const int it = threadIdx.x + NT * u;
+      const int c = it / (OZ_CHUNK / 2), rp = 2 * (it % (OZ_CHUNK / 2));
+#pragma unroll
+      for (int q = 0; q < 2 * E; ++q) pre[u][q] = 0.0;
+      if (it < ITEMS && c < bb) {
+        const double* col = Y + (size_t)pc.gcol(c) * E * ld;
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          if (c0 + rp + h < r1) {
+            if constexpr (CPLX) {
+              const double2 v = reinterpret_cast<const double2*>(col)[c0 + rp + h];
+              pre[u][h] = v.x;
+              pre[u][2 + h] = v.y;
+            } else {
+              pre[u][h] = col[c0 + rp + h];
+            }
+          }
+      }
+    }
+  };
+  if (r0 < r1) fetch(r0);
+  for (int c0 = r0; c0 < r1; c0 += OZ_CHUNK) {
+#pragma unroll
+    for (int u = 0; u < PERT; ++u) {
+      const int it = threadIdx.x + NT * u;
+      if (it >= ITEMS) continue;
+      const int c = it / (OZ_CHUNK / 2), rp = 2 * (it % (OZ_CHUNK / 2));
+#pragma unroll
+      for (int part = 0; part < E; ++part) {
         // complex column c (< bb) gives real-view columns c (Re) and bb + c
         // (Im); for c >= bb the zero columns 2c and 2c + 1 (they cover the
         // padding [2 bb, V))
-        double2 v0 = make_double2(0.0, 0.0), v1 = make_double2(0.0, 0.0);
-        if (c < bb) {
-          const double2* col = reinterpret_cast<const double2*>(Y) + (size_t)pc.gcol(c) * ld;
-          if (c0 + rp < r1) v0 = col[c0 + rp];
-          if (c0 + rp + 1 < r1) v1 = col[c0 + rp + 1];
-        }
-        const int cr = c < bb ? c : 2 * c, ci = c < bb ? bb + c : 2 * c + 1;
-        const int er = s_emax[cr], ei = s_emax[ci];
-        slice7(v0.x, er, 0, s0);
-        slice7(v1.x, er, 0, s1);
+        int vc = c;
+        if constexpr (CPLX) vc = part == 0 ? (c < bb ? c : 2 * c) : (c < bb ? bb + c : 2 * c + 1);
+        const int em = s_emax[vc];
+        uint32_t s0[NSL], s1[NSL];
+        slice7(pre[u][2 * part], em, 0, s0);
+        slice7(pre[u][2 * part + 1], em, 0, s1);
 #pragma unroll
-        for (int a = 0; a < NSL; ++a)
-          *reinterpret_cast<uint32_t*>(&Ss[a][cr][rp]) = (uint32_t)s0[a] | ((uint32_t)s1[a] << 16);
-        slice7(v0.y, ei, 0, s0);
-        slice7(v1.y, ei, 0, s1);
-#pragma unroll
-        for (int a = 0; a < NSL; ++a)
-          *reinterpret_cast<uint32_t*>(&Ss[a][ci][rp]) = (uint32_t)s0[a] | ((uint32_t)s1[a] << 16);
+        for (int a = 0; a < NSL; ++a) *reinterpret_cast<uint32_t*>(&Ss[a][vc][rp]) = s0[a] | (s1[a] << 16);
       }
     }
+    if (c0 + OZ_CHUNK < r1) fetch(c0 + OZ_CHUNK);
     __syncthreads();
     float acc[NLV][4];
 #pragma unroll
@@ -281,14 +330,11 @@ __global__ void __launch_bounds__(32 * oz_gram_warps<V>()) k_gram_oz(BlkDims d, 
   for (int q = 0; q < 4; ++q) {
     const int i = 16 * mt + g + ((q & 2) ? 8 : 0);
     const int j = 8 * nt + 2 * t + (q & 1);
-    __int128 T = 0;
+    long long x[NLV];
 #pragma unroll
-    for (int L = 0; L < NLV; ++L) {
-      const long long x = __float2ll_rn(hi[L][q]) + __float2ll_rn(lo[L][q]);
-      T += (__int128)x << (8 * (NLV - 1 - L));
-    }
+    for (int L = 0; L < NLV; ++L) x[L] = float_int_to_ll(hi[L][q]) + (long long)__float2int_rn(lo[L][q]);
     const int e2 = (s_emax[i] - 1022) + (s_emax[j] - 1022) - 64;
-    out[i * V + j] = i128_to_double(T, e2);
+    out[i * V + j] = levels_to_double(x, e2);
   }
 }
 
@@ -303,7 +349,6 @@ __global__ void __launch_bounds__(256) k_apply_oz(BlkDims d, BlkBuffers b, int s
   constexpr int YS = V + 8;  // padded row stride of the Y slices (bf16)
   constexpr int TS = V + 8;  // padded stride of a Z slice column (bf16)
   constexpr int NNW = V / 16;  // column tiles (n8) per warp
-  constexpr int PER = V * ATR / 256;  // real-view values per thread
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint16_t* Ys = reinterpret_cast<uint16_t*>(smem_raw);  // [NSL][ATR][YS]
   uint16_t* Ts = Ys + NSL * ATR * YS;                    // [NSL][V][TS]
@@ -332,49 +377,48 @@ __global__ void __launch_bounds__(256) k_apply_oz(BlkDims d, BlkBuffers b, int s
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
   // 1. Z-tilde into shared memory; the tile's real view into registers:
-  //    value i of thread x is row (x + 256 i) % 64 of real-view column
-  //    (x + 256 i) / 64 (complex: complex column (x + 256 i) / 64 gives the
-  //    values i (Re) and PER / 2 + i (Im))
+  //    thread x holds row x % 64 of the real-view column pairs
+  //    (2 (x / 64 + 4 i), 2 (x / 64 + 4 i) + 1), i = 0 .. V / 8 - 1
+  //    (complex: complex column x / 64 + 4 i gives real-view columns
+  //    c (Re) and bb + c (Im), or the zero columns 2c, 2c + 1 for c >= bb)
+  constexpr int NPR = V / 8;  // column pairs per thread
   for (int idx = threadIdx.x; idx < V * V; idx += 256) Zd[idx] = zt[idx];
   if (threadIdx.x < V) s_ey[threadIdx.x] = 1;
-  double y[PER];
-  const int rr = threadIdx.x & (ATR - 1);
-  if constexpr (!CPLX) {
+  const int rr = threadIdx.x & (ATR - 1), grp = threadIdx.x >> 6;
+  const bool live = r0 + rr < m;
+  double y[NPR][2];
+  int yc[NPR][2];  // real-view columns of the two values
 #pragma unroll
-    for (int i = 0; i < PER; ++i) {
-      const int c = (threadIdx.x + 256 * i) / ATR;
-      y[i] = (c < bb && r0 + rr < m) ? Y[(size_t)pc.gcol(c) * ld + r0 + rr] : 0.0;
-    }
-  } else {
+  for (int i = 0; i < NPR; ++i) {
+    if constexpr (!CPLX) {
+      const int c = 2 * (grp + 4 * i);
 #pragma unroll
-    for (int i = 0; i < PER / 2; ++i) {
-      const int c = (threadIdx.x + 256 * i) / ATR;
+      for (int h = 0; h < 2; ++h) {
+        yc[i][h] = c + h;
+        y[i][h] = (c + h < bb && live) ? Y[(size_t)pc.gcol(c + h) * ld + r0 + rr] : 0.0;
+      }
+    } else {
+      const int c = grp + 4 * i;
       double2 v = make_double2(0.0, 0.0);
-      if (c < bb && r0 + rr < m) v = reinterpret_cast<const double2*>(Y)[(size_t)pc.gcol(c) * ld + r0 + rr];
-      y[i] = v.x;
-      y[PER / 2 + i] = v.y;
+      if (c < bb && live) v = reinterpret_cast<const double2*>(Y)[(size_t)pc.gcol(c) * ld + r0 + rr];
+      y[i][0] = v.x;
+      y[i][1] = v.y;
+      yc[i][0] = c < bb ? c : 2 * c;
+      yc[i][1] = c < bb ? bb + c : 2 * c + 1;
     }
   }
   __syncthreads();
-  // real-view column of value i
-  auto vcol = [&](int i) -> int {
-    if constexpr (!CPLX) {
-      return (threadIdx.x + 256 * i) / ATR;
-    } else {
-      const int ii = i < PER / 2 ? i : i - PER / 2;
-      const int c = (threadIdx.x + 256 * ii) / ATR;
-      if (i < PER / 2) return c < bb ? c : 2 * c;
-      return c < bb ? bb + c : 2 * c + 1;
-    }
-  };
   // 2. column exponents of the tile (two warps share a column: 64 rows)
 #pragma unroll
-  for (int i = 0; i < PER; ++i) {
-    const int mx = __reduce_max_sync(FULL, exp_field(y[i]));
-    if (lane == 0) atomicMax(&s_ey[vcol(i)], mx);
-  }
+  for (int i = 0; i < NPR; ++i)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int mx = __reduce_max_sync(FULL, exp_field(y[i][h]));
+      if (lane == 0) atomicMax(&s_ey[yc[i][h]], mx);
+    }
   __syncthreads();
   // 3. Z' = D Z-tilde (row k scaled by 2^(e_k)), its column exponents, slices
+  //    (row pairs (k, k + 1) of a column packed in one word)
   for (int j = warp; j < V; j += 8) {
     int mx = 1;
     for (int k = lane; k < V; k += 32) {
@@ -385,20 +429,30 @@ __global__ void __launch_bounds__(256) k_apply_oz(BlkDims d, BlkBuffers b, int s
     if (lane == 0) s_fz[j] = mx;
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < V * V; idx += 256) {
-    const int k = idx / V, j = idx % V;
-    uint16_t sl[NSL];
-    slice7(Zd[idx], s_fz[j], s_ey[k] - 1022, sl);
+  for (int it = threadIdx.x; it < V * (V / 2); it += 256) {
+    const int j = it % V, k = 2 * (it / V);
+    uint32_t s0[NSL], s1[NSL];
+    slice7(Zd[k * V + j], s_fz[j], s_ey[k] - 1022, s0);
+    slice7(Zd[(k + 1) * V + j], s_fz[j], s_ey[k + 1] - 1022, s1);
 #pragma unroll
-    for (int a = 0; a < NSL; ++a) Ts[(a * V + j) * TS + k] = sl[a];
+    for (int a = 0; a < NSL; ++a) *reinterpret_cast<uint32_t*>(&Ts[(a * V + j) * TS + k]) = s0[a] | (s1[a] << 16);
   }
 #pragma unroll
-  for (int i = 0; i < PER; ++i) {
-    const int c = vcol(i);
-    uint16_t sl[NSL];
-    slice7(y[i], s_ey[c], 0, sl);
+  for (int i = 0; i < NPR; ++i) {
+    uint32_t s0[NSL], s1[NSL];
+    slice7(y[i][0], s_ey[yc[i][0]], 0, s0);
+    slice7(y[i][1], s_ey[yc[i][1]], 0, s1);
+    if constexpr (!CPLX) {
 #pragma unroll
-    for (int a = 0; a < NSL; ++a) Ys[(a * ATR + rr) * YS + c] = sl[a];
+      for (int a = 0; a < NSL; ++a)
+        *reinterpret_cast<uint32_t*>(&Ys[(a * ATR + rr) * YS + yc[i][0]]) = s0[a] | (s1[a] << 16);
+    } else {
+#pragma unroll
+      for (int a = 0; a < NSL; ++a) {
+        Ys[(a * ATR + rr) * YS + yc[i][0]] = (uint16_t)s0[a];
+        Ys[(a * ATR + rr) * YS + yc[i][1]] = (uint16_t)s1[a];
+      }
+    }
   }
   __syncthreads();
 
@@ -446,10 +500,10 @@ __global__ void __launch_bounds__(256) k_apply_oz(BlkDims d, BlkBuffers b, int s
     for (int q = 0; q < 4; ++q) {
       const int r = 16 * mt + g + ((q & 2) ? 8 : 0);
       const int j = 8 * (nt0 + u) + 2 * t + (q & 1);
-      __int128 T = 0;
+      long long x[NLV];
 #pragma unroll
-      for (int L = 0; L < NLV; ++L) T += (__int128)__float2int_rn(acc[u][L][q]) << (8 * (NLV - 1 - L));
-      Ob[j * OS + r] = i128_to_double(T, s_fz[j] - 1022 - 64);
+      for (int L = 0; L < NLV; ++L) x[L] = __float2int_rn(acc[u][L][q]);
+      Ob[j * OS + r] = levels_to_double(x, s_fz[j] - 1022 - 64);
     }
   __syncthreads();
   if constexpr (!CPLX) {
