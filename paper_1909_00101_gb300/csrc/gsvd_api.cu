@@ -438,8 +438,16 @@ size_t shortened_offset(const gsvd_config& cfg, int64_t n) {
   make_plan(cfg, GSVD_R64, n, n, n, S);
   return (S.total + 255) & ~size_t(255);
 }
+// digit planes of the tensor-core products (fp64_gemm = 1): the largest of
+// the Grams F^T F (n x n over m rows) and the products m x n x n
+size_t shortened_oz_bytes(const gsvd_config& cfg, int64_t mf, int64_t mg, int64_t n) {
+  if (cfg.fp64_gemm != 1) return 0;
+  const int m = (int)std::max(mf, mg);
+  return std::max(dgemm_oz_ws_bytes((int)n, (int)n, m), dgemm_oz_ws_bytes(m, (int)n, (int)n));
+}
 size_t shortened_total(const gsvd_config& cfg, int64_t mf, int64_t mg, int64_t n) {
-  return shortened_offset(cfg, n) + sizeof(double) * (4 * (size_t)n * n + (size_t)std::max(mf, mg) * n) + 256;
+  return shortened_offset(cfg, n) + sizeof(double) * (4 * (size_t)n * n + (size_t)std::max(mf, mg) * n) + 256 +
+         shortened_oz_bytes(cfg, mf, mg, n);
 }
 
 // device bytes one solve needs
@@ -565,16 +573,20 @@ int solve_shortened(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* in
   double* R1G = R1F + nn;
   double* T = R1G + nn;
   int* flag = reinterpret_cast<int*>(T + tmp);
+  OzWs ozw;
+  ozw.bytes = shortened_oz_bytes(cfg, mf, mg, n);
+  ozw.p = ozw.bytes ? reinterpret_cast<unsigned char*>(flag) + 256 : nullptr;
+  const OzWs* oz = ozw.bytes ? &ozw : nullptr;
   int hflag[2];
   const long long l0 = qr_launch_count();
   CK(cudaMemsetAsync(flag, 0, 8, s));
   CK(launch_check_finite(mf, n, false, F, p->ldf, flag + 1, s));
   CK(launch_check_finite(mg, n, false, G, p->ldg, flag + 1, s));
   // first pass: Grams and Choleskys; F and G are not modified yet
-  CK(dgemm(true, false, n, n, mf, 1.0, F, p->ldf, F, p->ldf, 0.0, R1F, n, true, s));
-  CK(potrf_upper(n, R1F, n, flag, s));
-  CK(dgemm(true, false, n, n, mg, 1.0, G, p->ldg, G, p->ldg, 0.0, R1G, n, true, s));
-  CK(potrf_upper(n, R1G, n, flag, s));
+  CK(dgemm(true, false, n, n, mf, 1.0, F, p->ldf, F, p->ldf, 0.0, R1F, n, true, s, oz));
+  CK(potrf_upper(n, R1F, n, flag, s, oz));
+  CK(dgemm(true, false, n, n, mg, 1.0, G, p->ldg, G, p->ldg, 0.0, R1G, n, true, s, oz));
+  CK(potrf_upper(n, R1G, n, flag, s, oz));
   CK(cudaMemcpyAsync(hflag, flag, 8, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (hflag[1]) return GSVD_EINVAL;
@@ -583,30 +595,30 @@ int solve_shortened(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* in
     return SHORT_SKIP;
   }
   // Q1 = F R1^{-1}; second pass R2 = chol(Q1^T Q1), Q = Q1 R2^{-1}
-  CK(trsm_right_upper(mf, n, R1F, n, F, p->ldf, s));
-  CK(trsm_right_upper(mg, n, R1G, n, G, p->ldg, s));
-  CK(dgemm(true, false, n, n, mf, 1.0, F, p->ldf, F, p->ldf, 0.0, RF, n, true, s));
-  CK(potrf_upper(n, RF, n, flag, s));
-  CK(dgemm(true, false, n, n, mg, 1.0, G, p->ldg, G, p->ldg, 0.0, RG, n, true, s));
-  CK(potrf_upper(n, RG, n, flag, s));
+  CK(trsm_right_upper(mf, n, R1F, n, F, p->ldf, s, oz));
+  CK(trsm_right_upper(mg, n, R1G, n, G, p->ldg, s, oz));
+  CK(dgemm(true, false, n, n, mf, 1.0, F, p->ldf, F, p->ldf, 0.0, RF, n, true, s, oz));
+  CK(potrf_upper(n, RF, n, flag, s, oz));
+  CK(dgemm(true, false, n, n, mg, 1.0, G, p->ldg, G, p->ldg, 0.0, RG, n, true, s, oz));
+  CK(potrf_upper(n, RG, n, flag, s, oz));
   CK(cudaMemcpyAsync(hflag, flag, 8, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (hflag[0]) {
     // Q1^T Q1 not numerically positive definite: undo (F = Q1 R1) and skip
-    CK(dgemm(false, false, mf, n, n, 1.0, F, p->ldf, R1F, n, 0.0, T, mf, false, s));
+    CK(dgemm(false, false, mf, n, n, 1.0, F, p->ldf, R1F, n, 0.0, T, mf, false, s, oz));
     CK(cudaMemcpy2DAsync(F, p->ldf * 8, T, (size_t)mf * 8, (size_t)mf * 8, n, cudaMemcpyDeviceToDevice, s));
-    CK(dgemm(false, false, mg, n, n, 1.0, G, p->ldg, R1G, n, 0.0, T, mg, false, s));
+    CK(dgemm(false, false, mg, n, n, 1.0, G, p->ldg, R1G, n, 0.0, T, mg, false, s, oz));
     CK(cudaMemcpy2DAsync(G, p->ldg * 8, T, (size_t)mg * 8, (size_t)mg * 8, n, cudaMemcpyDeviceToDevice, s));
     info->shorten_skipped = 1;
     return SHORT_SKIP;
   }
-  CK(trsm_right_upper(mf, n, RF, n, F, p->ldf, s));
-  CK(trsm_right_upper(mg, n, RG, n, G, p->ldg, s));
+  CK(trsm_right_upper(mf, n, RF, n, F, p->ldf, s, oz));
+  CK(trsm_right_upper(mg, n, RG, n, G, p->ldg, s, oz));
   // R = R2 R1 (both upper triangular)
-  CK(dgemm(false, false, n, n, n, 1.0, RF, n, R1F, n, 0.0, T, n, 2, s));
+  CK(dgemm(false, false, n, n, n, 1.0, RF, n, R1F, n, 0.0, T, n, 2, s, oz));
   CK(launch_zero_lower(n, T, n, s));
   CK(cudaMemcpyAsync(RF, T, nn * 8, cudaMemcpyDeviceToDevice, s));
-  CK(dgemm(false, false, n, n, n, 1.0, RG, n, R1G, n, 0.0, T, n, 2, s));
+  CK(dgemm(false, false, n, n, n, 1.0, RG, n, R1G, n, 0.0, T, n, 2, s, oz));
   CK(launch_zero_lower(n, T, n, s));
   CK(cudaMemcpyAsync(RG, T, nn * 8, cudaMemcpyDeviceToDevice, s));
   // the sweeps on the shortened pair
@@ -622,9 +634,9 @@ int solve_shortened(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* in
   const int st = solve_plain(c2, &sub, info, ws, h_ctr, s);
   if (st == GSVD_EINVAL || st == GSVD_ECUDA || st == GSVD_ENOMEM) return st;
   // U = Q_F U'', V = Q_G V''
-  CK(dgemm(false, false, mf, n, n, 1.0, F, p->ldf, RF, n, 0.0, T, mf, false, s));
+  CK(dgemm(false, false, mf, n, n, 1.0, F, p->ldf, RF, n, 0.0, T, mf, false, s, oz));
   CK(cudaMemcpy2DAsync(F, p->ldf * 8, T, (size_t)mf * 8, (size_t)mf * 8, n, cudaMemcpyDeviceToDevice, s));
-  CK(dgemm(false, false, mg, n, n, 1.0, G, p->ldg, RG, n, 0.0, T, mg, false, s));
+  CK(dgemm(false, false, mg, n, n, 1.0, G, p->ldg, RG, n, 0.0, T, mg, false, s, oz));
   CK(cudaMemcpy2DAsync(G, p->ldg * 8, T, (size_t)mg * 8, (size_t)mg * 8, n, cudaMemcpyDeviceToDevice, s));
   CK(cudaStreamSynchronize(s));
   info->shortened = 1;

@@ -120,20 +120,35 @@ cudaError_t launch_gemm_f64_by_f32(int m, int n, bool cplx, const double* A, lon
 // Z64 = diag(zdiag) * Z32 (rows scaled), FP64 result
 cudaError_t launch_rowscale(int n, bool cplx, const double* zdiag, const float* Z32, long long ld32,
                             double* Z, long long ldz, cudaStream_t s);
-// FP64 DMMA GEMM: C = alpha op(A) op(B) + beta C (column-major); upper = 1:
+// workspace of the tensor-core products (digit planes); products with
+// M N K >= OZ_GEMM_MIN run there when it is large enough
+struct OzWs {
+  void* p;
+  size_t bytes;
+};
+constexpr double OZ_GEMM_MIN = 1073741824.0;  // 2^30
+// FP64 GEMM: C = alpha op(A) op(B) + beta C (column-major); upper = 1:
 // only tiles meeting C's upper triangle are computed; upper = 2: also op(A)
 // and op(B) are upper triangular (square), so each tile sums its k range only
 cudaError_t dgemm(bool ta, bool tb, int M, int N, int K, double alpha, const double* A, long long lda,
                   const double* B, long long ldb, double beta, double* C, long long ldc, int upper,
-                  cudaStream_t s);
+                  cudaStream_t s, const OzWs* oz = nullptr);
 // kernels launched so far by the calling thread's dgemm/potrf/trsm calls
 long long qr_launch_count();
+// the same product on the BF16 tensor cores with FP64 accuracy (operands
+// sliced once into digit planes in ws); cudaErrorInvalidValue if ws is
+// smaller than dgemm_oz_ws_bytes(M, N, K)
+size_t dgemm_oz_ws_bytes(int M, int N, int K);
+cudaError_t dgemm_oz(bool ta, bool tb, int M, int N, int K, double alpha, const double* A, long long lda,
+                     const double* B, long long ldb, double beta, double* C, long long ldc, int upper, void* ws,
+                     size_t ws_bytes, cudaStream_t s);
 // zero the strict lower triangle of an n x n matrix
 cudaError_t launch_zero_lower(int n, double* A, long long lda, cudaStream_t s);
 // blocked Cholesky A = R^T R in place (upper), *fail = 1 on a non-positive pivot
-cudaError_t potrf_upper(int n, double* A, long long lda, int* fail, cudaStream_t s);
+cudaError_t potrf_upper(int n, double* A, long long lda, int* fail, cudaStream_t s, const OzWs* oz = nullptr);
 // B (m x n) <- B R^{-1} for upper triangular R (n x n)
-cudaError_t trsm_right_upper(int m, int n, const double* R, long long ldr, double* B, long long ldb, cudaStream_t s);
+cudaError_t trsm_right_upper(int m, int n, const double* R, long long ldr, double* B, long long ldb, cudaStream_t s,
+                             const OzWs* oz = nullptr);
 // non-finite check of a column-major matrix: sets *flag = 1 on NaN/Inf
 cudaError_t launch_check_finite(int m, int n, bool cplx, const double* A, long long lda, int* flag,
                                 cudaStream_t s);

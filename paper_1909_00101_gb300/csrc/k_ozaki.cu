@@ -151,6 +151,20 @@ __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const 
 
 __device__ __forceinline__ uint32_t ld32(const uint16_t* p) { return *reinterpret_cast<const uint32_t*>(p); }
 
+// level products of one k-step with the A fragments loaded slice by slice
+// (fewer live registers): acc[a + b] += A_a B_b for a + b + 2 <= 8
+template <class LoadA>
+__device__ __forceinline__ void level_mmas_stream(float acc[NLV][4], LoadA load_a, const uint32_t B[NSL][2]) {
+#pragma unroll
+  for (int a = 0; a < NSL; ++a) {
+    uint32_t A[4];
+    load_a(a, A);
+#pragma unroll
+    for (int b = 0; b < NSL; ++b)
+      if (a + b + 2 <= 8) mma_bf16(acc[a + b], A, B[b]);
+  }
+}
+
 // level products of one k-step: acc[L - 2] += A_a B_b for a + b = L <= 8
 __device__ __forceinline__ void level_mmas(float acc[NLV][4], const uint32_t A[NSL][4], const uint32_t B[NSL][2]) {
 #pragma unroll
@@ -520,6 +534,182 @@ __global__ void __launch_bounds__(256) k_apply_oz(BlkDims d, BlkBuffers b, int s
   }
 }
 
+
+// ------------------------------------------------------ general DGEMM ----
+// C = alpha op(A) op(B) + beta C (column-major FP64) on the BF16 tensor
+// cores with FP64 accuracy, for the large products of the QR shortening.
+// Each operand is sliced once into digit planes: for every row r of op(A)
+// (every column of op(B)) one scale, the exponent field e[r] of its largest
+// |value| over all of K, and S[p][r][k] = BF16 digit p of value (r, k),
+// k < Kp = K rounded up to 32 (zero beyond K).  The product kernel then
+// runs on 32 x 32 output tiles, K in chunks of 32 (exact FP32 level sums),
+// flushed into exact FP32 double-words (TwoSum) and rounded once to FP64.
+
+// rows whose k values are contiguous: value (r, k) = X[r ld + k]; one warp per row
+__global__ void __launch_bounds__(256) k_slice_kc(int R, int K, const double* __restrict__ X, long long ld,
+                                                  uint16_t* __restrict__ S, long long Kp, long long plane,
+                                                  int* __restrict__ e) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = blockIdx.x * 8 + warp;
+  if (r >= R) return;
+  const double* row = X + (size_t)r * ld;
+  int mx = 1;
+  for (int k = lane; k < K; k += 32) mx = max(mx, exp_field(row[k]));
+  mx = __reduce_max_sync(FULL, mx);
+  if (lane == 0) e[r] = mx;
+  uint16_t* out = S + (size_t)r * Kp;
+  for (int k = 2 * lane; k < Kp; k += 64) {
+    const double x0 = k < K ? row[k] : 0.0, x1 = k + 1 < K ? row[k + 1] : 0.0;
+    uint32_t s0[NSL], s1[NSL];
+    slice7(x0, mx, 0, s0);
+    slice7(x1, mx, 0, s1);
+#pragma unroll
+    for (int q = 0; q < NSL; ++q) *reinterpret_cast<uint32_t*>(out + q * plane + k) = s0[q] | (s1[q] << 16);
+  }
+}
+
+// rows that are strided: value (r, k) = X[k ld + r] (the rows of a
+// column-major matrix); 32 rows per CTA, transposed through shared memory
+__global__ void __launch_bounds__(256) k_slice_tr(int R, int K, const double* __restrict__ X, long long ld,
+                                                  uint16_t* __restrict__ S, long long Kp, long long plane,
+                                                  int* __restrict__ e) {
+  __shared__ double T[32][33];
+  __shared__ int s_e[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r0 = blockIdx.x * 32, r = r0 + lane;
+  const bool live = r < R;
+  if (threadIdx.x < 32) s_e[threadIdx.x] = 1;
+  int mx = 1;
+  if (live)
+    for (int k = warp; k < K; k += 8) mx = max(mx, exp_field(X[(size_t)k * ld + r]));
+  __syncthreads();
+  atomicMax(&s_e[lane], mx);
+  __syncthreads();
+  if (warp == 0 && live) e[r] = s_e[lane];
+  for (int k0 = 0; k0 < Kp; k0 += 32) {
+    for (int kk = warp; kk < 32; kk += 8) T[kk][lane] = (live && k0 + kk < K) ? X[(size_t)(k0 + kk) * ld + r] : 0.0;
+    __syncthreads();
+    for (int rr = warp; rr < 32; rr += 8) {
+      if (r0 + rr < R && lane < 16) {
+        const int kk = 2 * lane;
+        uint32_t s0[NSL], s1[NSL];
+        slice7(T[kk][rr], s_e[rr], 0, s0);
+        slice7(T[kk + 1][rr], s_e[rr], 0, s1);
+        uint16_t* out = S + (size_t)(r0 + rr) * Kp + k0 + kk;
+#pragma unroll
+        for (int q = 0; q < NSL; ++q) *reinterpret_cast<uint32_t*>(out + q * plane) = s0[q] | (s1[q] << 16);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = valid ? 16 : 0;  // 0: the 16 bytes are zero-filled, nothing is read
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+constexpr int GT = 32;  // output tile edge of the general product
+
+// one warp per m16 x n8 tile of the 32 x 32 output: rows 16 (w >> 2), columns 8 (w & 3)
+__global__ void __launch_bounds__(256, 2) k_gemm_oz(int M, int N, int K, long long Kp, const uint16_t* __restrict__ As,
+                                                 long long aplane, const uint16_t* __restrict__ Bs, long long bplane,
+                                                 const int* __restrict__ ea, const int* __restrict__ eb, double alpha,
+                                                 double beta, double* __restrict__ C, long long ldc, int upper) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // [stage][operand][slice][row][GRS]
+  uint16_t* sm = reinterpret_cast<uint16_t*>(smem_raw);
+  auto at = [&](int st, int op, int q, int row) -> uint16_t* {
+    return sm + ((((size_t)st * 2 + op) * NSL + q) * GT + row) * GRS;
+  };
+  const int m0 = blockIdx.x * GT, n0 = blockIdx.y * GT;
+  if (upper && m0 >= n0 + GT) return;  // below the diagonal: not needed
+  const int kbeg = upper == 2 ? m0 : 0;
+  const int kend = upper == 2 ? min(K, n0 + GT) : K;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int mt = warp >> 2, nt = warp & 3, g = lane >> 2, t = lane & 3;
+  // copies of one chunk: 2 operands x 7 slices x 32 rows x 4 pieces of 16 bytes
+  auto issue = [&](int st, int k0) {
+    for (int c = threadIdx.x; c < 2 * NSL * GT * 4; c += 256) {
+      const int piece = c & 3, row = (c >> 2) % GT, q = (c >> 2) / GT % NSL, op = c / (NSL * GT * 4);
+      const int rr = (op ? n0 : m0) + row;
+      const bool valid = rr < (op ? N : M);
+      const uint16_t* base = op ? Bs + q * bplane : As + q * aplane;
+      const uint16_t* src = valid ? base + (size_t)rr * Kp + k0 + piece * 8 : base;
+      cp_async16(at(st, op, q, row) + piece * 8, src, valid);
+    }
+    cp_async_commit();
+  };
+  float hi[NLV][4], lo[NLV][4];
+#pragma unroll
+  for (int L = 0; L < NLV; ++L)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) hi[L][q] = lo[L][q] = 0.0f;
+  int st = 0;
+  if (kbeg < kend) issue(0, kbeg);
+  for (int k0 = kbeg; k0 < kend; k0 += OZ_CHUNK) {
+    if (k0 + OZ_CHUNK < kend) {
+      issue(st ^ 1, k0 + OZ_CHUNK);
+      cp_async_wait_1();
+    } else {
+      cp_async_wait_0();
+    }
+    __syncthreads();
+    float acc[NLV][4];
+#pragma unroll
+    for (int L = 0; L < NLV; ++L)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[L][q] = 0.0f;
+#pragma unroll
+    for (int kb = 0; kb < OZ_CHUNK; kb += 16) {
+      uint32_t B[NSL][2];
+#pragma unroll
+      for (int q = 0; q < NSL; ++q) {
+        const uint16_t* bp = at(st, 1, q, 8 * nt + g);
+        B[q][0] = ld32(bp + kb + 2 * t);
+        B[q][1] = ld32(bp + kb + 2 * t + 8);
+      }
+      auto load_a = [&](int q, uint32_t A[4]) {
+        const uint16_t* ap = at(st, 0, q, 16 * mt + g);
+        A[0] = ld32(ap + kb + 2 * t);
+        A[1] = ld32(ap + 8 * GRS + kb + 2 * t);
+        A[2] = ld32(ap + kb + 2 * t + 8);
+        A[3] = ld32(ap + 8 * GRS + kb + 2 * t + 8);
+      };
+      level_mmas_stream(acc, load_a, B);
+    }
+#pragma unroll
+    for (int L = 0; L < NLV; ++L)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float x = acc[L][q], h = hi[L][q];
+        const float sum = h + x;
+        const float bv = sum - h;
+        const float err = (h - (sum - bv)) + (x - bv);
+        hi[L][q] = sum;
+        lo[L][q] += err;
+      }
+    __syncthreads();  // this stage is refilled by the next issue
+    st ^= 1;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = m0 + 16 * mt + g + ((q & 2) ? 8 : 0);
+    const int j = n0 + 8 * nt + 2 * t + (q & 1);
+    if (i >= M || j >= N) continue;
+    long long x[NLV];
+#pragma unroll
+    for (int L = 0; L < NLV; ++L) x[L] = float_int_to_ll(hi[L][q]) + (long long)__float2int_rn(lo[L][q]);
+    const double v = levels_to_double(x, (ea[i] - 1022) + (eb[j] - 1022) - 64);
+    double* cp = C + (size_t)j * ldc + i;
+    *cp = beta == 0.0 ? alpha * v : fma(alpha, v, beta * *cp);
+  }
+}
+
 template <int V>
 size_t apply_oz_smem() {
   const size_t slices = sizeof(uint16_t) * NSL * ((size_t)ATR * (V + 8) + (size_t)V * (V + 8));
@@ -565,6 +755,58 @@ cudaError_t launch_apply_oz(const BlkDims& d, const BlkBuffers& b, bool cplx, in
   if (V == 16) return cplx ? apply_oz_v<16, true>(d, b, step, s) : apply_oz_v<16, false>(d, b, step, s);
   if (V == 32) return cplx ? apply_oz_v<32, true>(d, b, step, s) : apply_oz_v<32, false>(d, b, step, s);
   return cudaErrorInvalidValue;
+}
+
+
+static size_t align256z(size_t x) { return (x + 255) & ~size_t(255); }
+
+size_t dgemm_oz_ws_bytes(int M, int N, int K) {
+  const size_t Kp = (size_t)(K + 31) / 32 * 32;
+  return align256z(sizeof(uint16_t) * NSL * (size_t)M * Kp) + align256z(sizeof(uint16_t) * NSL * (size_t)N * Kp) +
+         align256z(sizeof(int) * ((size_t)M + N)) + 256;
+}
+
+cudaError_t dgemm_oz(bool ta, bool tb, int M, int N, int K, double alpha, const double* A, long long lda,
+                     const double* B, long long ldb, double beta, double* C, long long ldc, int upper, void* ws,
+                     size_t ws_bytes, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (!ws || ws_bytes < dgemm_oz_ws_bytes(M, N, K) || K <= 0) return cudaErrorInvalidValue;
+  const long long Kp = (long long)(K + 31) / 32 * 32;
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  uint16_t* As = reinterpret_cast<uint16_t*>(w);
+  w += align256z(sizeof(uint16_t) * NSL * (size_t)M * Kp);
+  uint16_t* Bs = reinterpret_cast<uint16_t*>(w);
+  w += align256z(sizeof(uint16_t) * NSL * (size_t)N * Kp);
+  int* ea = reinterpret_cast<int*>(w);
+  int* eb = ea + M;
+  const long long aplane = (long long)M * Kp, bplane = (long long)N * Kp;
+  // the Gram op(A) = A^T, op(B) = A slices the same rows once
+  const bool same = ta && !tb && A == B && lda == ldb && M == N;
+  // rows of op(A): columns of A (ta) or rows of A; columns of op(B): columns of B (!tb) or rows of B
+  if (ta)
+    k_slice_kc<<<(M + 7) / 8, 256, 0, s>>>(M, K, A, lda, As, Kp, aplane, ea);
+  else
+    k_slice_tr<<<(M + 31) / 32, 256, 0, s>>>(M, K, A, lda, As, Kp, aplane, ea);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (same) {
+    Bs = As;
+    eb = ea;
+  } else {
+    if (!tb)
+      k_slice_kc<<<(N + 7) / 8, 256, 0, s>>>(N, K, B, ldb, Bs, Kp, bplane, eb);
+    else
+      k_slice_tr<<<(N + 31) / 32, 256, 0, s>>>(N, K, B, ldb, Bs, Kp, bplane, eb);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  const size_t smem = sizeof(uint16_t) * 2 * 2 * NSL * GT * GRS;
+  e = cudaFuncSetAttribute(k_gemm_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((M + GT - 1) / GT, (N + GT - 1) / GT);
+  k_gemm_oz<<<grid, 256, smem, s>>>(M, N, K, Kp, As, aplane, Bs, same ? aplane : bplane, ea, eb, alpha, beta, C,
+                                    ldc, upper);
+  return cudaGetLastError();
 }
 
 }  // namespace hz

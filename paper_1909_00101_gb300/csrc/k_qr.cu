@@ -8,7 +8,9 @@
 // Q = Q1 R2^{-1}, R = R2 R1) built from FP64 kernels: a DMMA GEMM, a blocked
 // right-looking Cholesky (one-CTA diagonal blocks, row-panel triangular
 // solves, GEMM trailing updates) and a blocked right triangular solve with
-// row-wise substitution (backward stable per row).  It is accurate for
+// row-wise substitution (backward stable per row); the large products run on
+// the BF16 tensor cores with FP64 accuracy (k_ozaki.cu) when the caller
+// gives a workspace for the digit planes.  It is accurate for
 // cond(F) up to about 1e8; the caller skips the shortening when the first
 // Cholesky of either Gram fails.  Real data only.
 #include <algorithm>
@@ -177,8 +179,18 @@ long long qr_launch_count() { return t_launches; }
 
 cudaError_t dgemm(bool ta, bool tb, int M, int N, int K, double alpha, const double* A, long long lda,
                   const double* B, long long ldb, double beta, double* C, long long ldc, int upper,
-                  cudaStream_t s) {
+                  cudaStream_t s, const OzWs* oz) {
   if (M <= 0 || N <= 0) return cudaSuccess;
+  // large products on the tensor cores (FP64 accuracy), small ones on DMMA.
+  // The sliced product bounds an entry's error by the largest |value| of its
+  // row of op(A) times that of its column of op(B); every product here has
+  // an op(A) with columns of one scale (Q, or F^T's rows as F's columns),
+  // except the triangular R2 R1 (upper = 2), which stays on DMMA.
+  if (oz && oz->p && upper != 2 && (double)M * N * K >= OZ_GEMM_MIN && oz->bytes >= dgemm_oz_ws_bytes(M, N, K)) {
+    const bool same = ta && !tb && A == B && lda == ldb && M == N;
+    t_launches += same ? 2 : 3;
+    return dgemm_oz(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, upper, oz->p, oz->bytes, s);
+  }
   dim3 grid((M + DM - 1) / DM, (N + DN - 1) / DN);
   ++t_launches;
   if (ta && !tb)
@@ -193,7 +205,7 @@ cudaError_t dgemm(bool ta, bool tb, int M, int N, int K, double alpha, const dou
 }
 
 // Blocked Cholesky A = R^T R in place (upper), strict lower part zeroed.
-cudaError_t potrf_upper(int n, double* A, long long lda, int* fail, cudaStream_t s) {
+cudaError_t potrf_upper(int n, double* A, long long lda, int* fail, cudaStream_t s, const OzWs* oz) {
   for (int k0 = 0; k0 < n; k0 += QB) {
     const int nb = std::min(QB, n - k0);
     double* Akk = A + (size_t)k0 * lda + k0;
@@ -205,7 +217,7 @@ cudaError_t potrf_upper(int n, double* A, long long lda, int* fail, cudaStream_t
       double* Akr = A + (size_t)(k0 + nb) * lda + k0;  // nb x rest block right of the diagonal
       k_trsm_lt<<<(rest + 127) / 128, 128, 0, s>>>(nb, rest, Akk, lda, Akr, lda);
       double* Arr = A + (size_t)(k0 + nb) * lda + k0 + nb;
-      cudaError_t e = dgemm(true, false, rest, rest, nb, -1.0, Akr, lda, Akr, lda, 1.0, Arr, lda, true, s);
+      cudaError_t e = dgemm(true, false, rest, rest, nb, -1.0, Akr, lda, Akr, lda, 1.0, Arr, lda, true, s, oz);
       if (e != cudaSuccess) return e;
     }
   }
@@ -223,7 +235,8 @@ cudaError_t launch_zero_lower(int n, double* A, long long lda, cudaStream_t s) {
 // B (m x n) <- B R^{-1}, R n x n upper: recursive halving (B1 R11^{-1}, then
 // B2 -= B1 R12, then B2 R22^{-1}) down to column blocks of QB, which the
 // row-wise substitution kernel solves; the bulk of the work is in the GEMMs.
-cudaError_t trsm_right_upper(int m, int n, const double* R, long long ldr, double* B, long long ldb, cudaStream_t s) {
+cudaError_t trsm_right_upper(int m, int n, const double* R, long long ldr, double* B, long long ldb, cudaStream_t s,
+                             const OzWs* oz) {
   if (m <= 0 || n <= 0) return cudaSuccess;
   if (n <= QB) {
     k_trsm_ru<<<(m + 127) / 128, 128, 0, s>>>(m, n, R, ldr, B, ldb);
@@ -231,12 +244,12 @@ cudaError_t trsm_right_upper(int m, int n, const double* R, long long ldr, doubl
     return cudaGetLastError();
   }
   const int n1 = ((n / 2 + QB - 1) / QB) * QB;
-  cudaError_t e = trsm_right_upper(m, n1, R, ldr, B, ldb, s);
+  cudaError_t e = trsm_right_upper(m, n1, R, ldr, B, ldb, s, oz);
   if (e != cudaSuccess) return e;
   double* B2 = B + (size_t)n1 * ldb;
-  e = dgemm(false, false, m, n - n1, n1, -1.0, B, ldb, R + (size_t)n1 * ldr, ldr, 1.0, B2, ldb, false, s);
+  e = dgemm(false, false, m, n - n1, n1, -1.0, B, ldb, R + (size_t)n1 * ldr, ldr, 1.0, B2, ldb, false, s, oz);
   if (e != cudaSuccess) return e;
-  return trsm_right_upper(m, n - n1, R + (size_t)n1 * ldr + n1, ldr, B2, ldb, s);
+  return trsm_right_upper(m, n - n1, R + (size_t)n1 * ldr + n1, ldr, B2, ldb, s, oz);
 }
 
 }  // namespace hz

@@ -102,11 +102,17 @@ def test_workspace_bytes_grows_with_size(lib):
     mixed = hz.make_config(path="blocked", precision="mixed", shorten=0)
     assert lib.gsvd_workspace_bytes(ctypes.byref(mixed), 0, 4096, 4096, 2048) > b
     # QR shortening (real, tall): the n x n sub-problem's workspace plus
-    # R_F, R_G, R1_F, R1_G (n^2 each) and a max(m_F, m_G) x n product buffer
-    sh = hz.make_config(path="blocked", shorten=1)
+    # R_F, R_G, R1_F, R1_G (n^2 each) and a max(m_F, m_G) x n product buffer,
+    # plus (fp64_gemm = 1) the BF16 digit planes of the largest product:
+    # 7 digits x 2 bytes for both n x m operands of the Gram F^T F
+    sh = hz.make_config(path="blocked", shorten=1, fp64_gemm=0)
     n, m = 2048, 4096
     sub = lib.gsvd_workspace_bytes(ctypes.byref(cfg), 0, n, n, n)
     got = lib.gsvd_workspace_bytes(ctypes.byref(sh), 0, m, m, n)
     assert got >= sub + 8 * (4 * n * n + m * n) and got <= sub + 8 * (4 * n * n + m * n) + 1024
+    shoz = hz.make_config(path="blocked", shorten=1, fp64_gemm=1)
+    got_oz = lib.gsvd_workspace_bytes(ctypes.byref(shoz), 0, m, m, n)
+    planes = 2 * 7 * 2 * n * m
+    assert planes <= got_oz - got <= planes + 65536  # + the per-row scale exponents
     # complex problems are not shortened
     assert lib.gsvd_workspace_bytes(ctypes.byref(sh), 1, m, m, n) == c
