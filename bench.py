@@ -145,6 +145,8 @@ def lib_kw(args) -> dict:
         kw["fp32_params"] = args.fp32_params
     if getattr(args, "fp64_gemm", None) is not None:
         kw["fp64_gemm"] = args.fp64_gemm
+    if getattr(args, "fp32_stop", None) is not None:
+        kw["fp32_stop_permille"] = args.fp32_stop
     return kw
 
 
@@ -403,6 +405,8 @@ def main():
                     help="2x2 parameters of the FP32 bulk sweeps in FP32 (1) or FP64 (0); default: library's")
     ap.add_argument("--fp64-gemm", type=int, default=None, choices=[0, 1],
                     help="FP64 Gram/apply on the BF16 tensor cores (1) or FP64 DMMA (0); default: library's")
+    ap.add_argument("--fp32-stop", type=int, default=None,
+                    help="FP32 sweeps stop below this many per mille big transformations; default: library's")
     ap.add_argument("--shorten", type=int, default=1, choices=[0, 1, 2],
                     help="QR shortening of Sec. 2: 0 never, 1 when m_F + m_G >= 2.6 n, 2 always")
     ap.add_argument("--compare", type=int, default=1, help="also time the other precision (1 step)")

@@ -91,6 +91,10 @@ typedef struct {
                                cores with FP64 accuracy (operands split into 8-bit integer slices,
                                exact level sums, one rounding; default, block widths with 2w <= 32
                                real / 4w <= 32 complex), 0 = FP64 DMMA */
+  int32_t fp32_stop_permille; /* mixed precision: the FP32 bulk sweeps stop (and the FP64 sweeps take
+                               over) after a sweep in which big transformations number fewer than
+                               this many per mille of the pivot pairs examined (default 50); 0 = run
+                               them to their own convergence (or fp32_max_sweeps) */
 } gsvd_config;
 
 /* One problem.  dtype = GSVD_R64 or GSVD_C128. */

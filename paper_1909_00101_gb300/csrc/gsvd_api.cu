@@ -356,6 +356,16 @@ int run_sweeps(const Plan& P, const gsvd_config& cfg, bool fp32, void* F, long l
       converged = true;
       break;
     }
+    // FP32 bulk sweeps hand over to the FP64 sweeps once few of their
+    // transformations are big: the FP64 sweep count no longer falls after
+    // that point, while every further FP32 sweep costs a full sweep
+    // (pairs examined in the sweep: pair visits x b (b - 1) / 2 x inner sweeps)
+    const double examined = (double)h_ctr[4] * (2.0 * P.w) * (2.0 * P.w - 1.0) * 0.5 * (double)ip.inner_max;
+    if (fp32 && cfg.fp32_stop_permille > 0 &&
+        (double)h_ctr[1] * 1000.0 < (double)cfg.fp32_stop_permille * examined) {
+      converged = true;
+      break;
+    }
     CK(launch_rescale(P.mf, P.mg, P.n, P.cplx, fp32, F, ldf, G, ldg, Z, ldz, s));
   }
   *sweeps_out = sw;
@@ -775,6 +785,7 @@ void gsvd_config_default(gsvd_config* c) {
   c->shorten = 1;
   c->fp32_params = 1;
   c->fp64_gemm = 1;
+  c->fp32_stop_permille = 50;
 }
 
 int gsvd_create(gsvd_handle* h, const gsvd_config* cfg, void* stream) {

@@ -243,9 +243,16 @@ __device__ __forceinline__ void unpack_upper(int u, int& i, int& j) {
 // only): the whole pivot-pair step in FP32 -- partial sums, Choleskys and
 // 2x2 parameters; its inputs are FP32 Gram partials, so FP32 arithmetic is as
 // accurate as they are.  Otherwise the sums and Choleskys are FP64.
+// Threads of the pivot kernel.
+template <bool P32>
+__host__ __device__ constexpr int inner_threads() {
+  return 512;
+}
+
 template <class Ti, class To, bool CPLX, int V, bool P32>
-__global__ void __launch_bounds__(512) k_inner(BlkDims d, BlkBuffers b, int step, InnerParams prm) {
+__global__ void __launch_bounds__(inner_threads<P32>()) k_inner(BlkDims d, BlkBuffers b, int step, InnerParams prm) {
   constexpr int E = CPLX ? 2 : 1;
+  constexpr int NTH = inner_threads<P32>();
   constexpr int BMAX = CPLX ? V / 2 : V;  // max columns of the pair
   using Tc = typename std::conditional<P32, float, double>::type;  // sums and Choleskys
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -408,7 +415,7 @@ __global__ void __launch_bounds__(512) k_inner(BlkDims d, BlkBuffers b, int step
 
   // 3. F-hat, G-hat (inner data type, in place), Z-hat = I
   {
-    Tc tmpA[E * BMAX * BMAX / 512 + 1], tmpB[E * BMAX * BMAX / 512 + 1];
+    Tc tmpA[E * BMAX * BMAX / NTH + 1], tmpB[E * BMAX * BMAX / NTH + 1];
     int cnt = 0;
     for (int idx = threadIdx.x; idx < E * bb * bb; idx += blockDim.x, ++cnt) {
       const int j = idx / (E * bb), i = (idx % (E * bb)) / E, part = idx % E;
@@ -459,6 +466,114 @@ __global__ void __launch_bounds__(512) k_inner(BlkDims d, BlkBuffers b, int step
   __syncthreads();
   for (int sw = 0; sw < prm.inner_max; ++sw) {
     int sweep_all = 0;
+    if constexpr (P32) {
+      // FP32 sweeps: each pair's warp takes its own 2x2 parameters (all lanes
+      // hold the four dot products after the reduction and compute the same
+      // FP32 values), so a step needs one barrier; counters per warp
+      int n_rot = 0, n_big = 0;
+      bool chg = false;
+      const float tolf = (float)tol;
+      for (int st = 0; st < M - 1; ++st) {
+        for (int k = warp; k < npairs; k += nwarps) {
+          const int i = s_pair[st][k][0], j = s_pair[st][k][1];
+          if (j >= bb) continue;
+          float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+          float w2[2] = {0.0f, 0.0f};
+          if constexpr (!CPLX) {
+            for (int r = lane; r < bb; r += 32) {
+              const float fi = Fh[i * bb + r], fj = Fh[j * bb + r];
+              v[0] += fi * fi;
+              v[1] += fj * fj;
+              v[2] += fi * fj;
+              v[3] += Gh[i * bb + r] * Gh[j * bb + r];
+            }
+            warp_sum4(v);
+          } else {
+            for (int r = lane; r < bb; r += 32) {
+              const float fir = Fh[2 * (i * bb + r)], fii = Fh[2 * (i * bb + r) + 1];
+              const float fjr = Fh[2 * (j * bb + r)], fji = Fh[2 * (j * bb + r) + 1];
+              const float gir = Gh[2 * (i * bb + r)], gii = Gh[2 * (i * bb + r) + 1];
+              const float gjr = Gh[2 * (j * bb + r)], gji = Gh[2 * (j * bb + r) + 1];
+              v[0] += fir * fir + fii * fii;
+              v[1] += fjr * fjr + fji * fji;
+              v[2] += fir * fjr + fii * fji;
+              v[3] += fir * fji - fii * fjr;
+              w2[0] += gir * gjr + gii * gji;
+              w2[1] += gir * gji - gii * gjr;
+            }
+            warp_sum4(v);
+            w2[0] = warp_sum(w2[0]);
+            w2[1] = warp_sum(w2[1]);
+          }
+          PivotOutT<float> o;
+          if constexpr (!CPLX)
+            o = pivot_real<float>(v[0], v[1], v[2], v[3], tolf, false, true, prm.crit2);
+          else
+            o = pivot_cplx<float>(v[0], v[1], v[2], v[3], w2[0], w2[1], tolf, prm.sort, true, prm.crit2);
+          const bool rot = o.flags & PV_ROT;
+          bool swp = o.flags & PV_SWAP;
+          if (o.flags & PV_FAIL) {
+            if (lane == 0) s_ctr[2] = 1;
+            continue;
+          }
+          if constexpr (!CPLX) {
+            // sort decision: transformed diagonal of A-hat (Sec. 3.5.3)
+            if (prm.sort) {
+              if (rot) {
+                const float d1 = o.z11 * o.z11 * v[0] + 2.0f * o.z11 * o.z21 * v[2] + o.z21 * o.z21 * v[1];
+                const float d2 = o.z12 * o.z12 * v[0] + 2.0f * o.z22 * o.z12 * v[2] + o.z22 * o.z22 * v[1];
+                swp = d1 < d2;
+              } else {
+                swp = v[0] < v[1];
+              }
+            }
+          }
+          n_rot += rot ? 1 : 0;
+          n_big += (o.flags & PV_BIG) ? 1 : 0;
+          chg = chg || rot || swp;
+          if (!rot && !swp) continue;
+          const float z11 = o.z11, z12 = o.z12, z21 = o.z21, z22 = o.z22, z12i = o.z12i, z21i = o.z21i;
+          auto upd = [&](float* Y) {
+            for (int r = lane; r < bb; r += 32) {
+              if constexpr (!CPLX) {
+                const float yi = Y[i * bb + r], yj = Y[j * bb + r];
+                float ni = yi, nj = yj;
+                if (rot) {
+                  ni = fmaf(yj, z21, yi * z11);
+                  nj = fmaf(yi, z12, yj * z22);
+                }
+                Y[i * bb + r] = swp ? nj : ni;
+                Y[j * bb + r] = swp ? ni : nj;
+              } else {
+                const float yir = Y[2 * (i * bb + r)], yii = Y[2 * (i * bb + r) + 1];
+                const float yjr = Y[2 * (j * bb + r)], yji = Y[2 * (j * bb + r) + 1];
+                float nir = yir, nii = yii, njr = yjr, nji = yji;
+                if (rot) {
+                  nir = fmaf(yjr, z21, fmaf(-yji, z21i, yir * z11));
+                  nii = fmaf(yjr, z21i, fmaf(yji, z21, yii * z11));
+                  njr = fmaf(yir, z12, fmaf(-yii, z12i, yjr * z22));
+                  nji = fmaf(yir, z12i, fmaf(yii, z12, yji * z22));
+                }
+                Y[2 * (i * bb + r)] = swp ? njr : nir;
+                Y[2 * (i * bb + r) + 1] = swp ? nji : nii;
+                Y[2 * (j * bb + r)] = swp ? nir : njr;
+                Y[2 * (j * bb + r) + 1] = swp ? nii : nji;
+              }
+            }
+          };
+          upd(reinterpret_cast<float*>(Fh));
+          upd(reinterpret_cast<float*>(Gh));
+          upd(reinterpret_cast<float*>(Zh));
+        }
+        __syncthreads();
+        if (s_ctr[2]) break;
+      }
+      if (lane == 0) {
+        if (n_rot) atomicAdd(&s_ctr[0], n_rot);
+        if (n_big) atomicAdd(&s_ctr[1], n_big);
+        if (chg) s_ctr[3] = 1;
+      }
+    } else
     for (int st = 0; st < M - 1; ++st) {
       for (int k = warp; k < npairs; k += nwarps) {
         const int i = s_pair[st][k][0], j = s_pair[st][k][1];
@@ -500,10 +615,9 @@ __global__ void __launch_bounds__(512) k_inner(BlkDims d, BlkBuffers b, int step
         }
       }
       __syncthreads();
-      // 2x2 parameters, one pair per lane (npairs <= 32).  FP64: real pivots
+      // 2x2 parameters in FP64, one pair per lane (npairs <= 32): real pivots
       // run their two independent chains on warps 0 and 1 (two SM
-      // sub-partitions), complex pivots on warp 0.  FP32 bulk sweeps with
-      // par32: the whole pivot in FP32 on warp 0.  Counters are
+      // sub-partitions), complex pivots on warp 0.  Counters are
       // warp-aggregated.
       auto count_flags = [&](int fl) {
         const unsigned rot = __ballot_sync(FULL, fl & PV_ROT), big = __ballot_sync(FULL, fl & PV_BIG);
@@ -515,32 +629,7 @@ __global__ void __launch_bounds__(512) k_inner(BlkDims d, BlkBuffers b, int step
           if (chg) s_ctr[3] = 1;
         }
       };
-      bool done32 = false;
-      if constexpr (P32) {
-        {
-          done32 = true;
-          if (warp == 0) {
-            const bool act = lane < npairs && s_pair[st][lane < npairs ? lane : 0][1] < bb;
-            int fl = 0;
-            if (act) {
-              const PivInT<Ti> p = pin[lane];
-              PivotOutT<float> o;
-              if constexpr (!CPLX)
-                o = pivot_real<float>(p.a11, p.a22, p.ar, p.br, (float)tol, false, true, prm.crit2);
-              else
-                o = pivot_cplx<float>(p.a11, p.a22, p.ar, p.ai, p.br, p.bi, (float)tol, prm.sort, true, prm.crit2);
-              PivZ<Ti> q;
-              q.z11 = o.z11; q.z12 = o.z12; q.z21 = o.z21; q.z22 = o.z22;
-              q.z12i = o.z12i; q.z21i = o.z21i;
-              q.flags = o.flags;
-              pout[lane] = q;
-              fl = o.flags;
-            }
-            count_flags(fl);
-          }
-        }
-      }
-      if (!done32 && warp <= 1) {
+      if (warp <= 1) {
         const bool act = lane < npairs && s_pair[st][lane < npairs ? lane : 0][1] < bb;
         int fl = 0;
         PivotOut o;
@@ -878,7 +967,7 @@ cudaError_t inner_v(const BlkDims& d, const BlkBuffers& b, int step, const Inner
   auto kern = (can32 && p.par32) ? k_inner<Ti, To, CPLX, V, can32> : k_inner<Ti, To, CPLX, V, false>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  kern<<<d.nslots, 512, smem, s>>>(d, b, step, p);
+  kern<<<d.nslots, (can32 && p.par32) ? inner_threads<true>() : inner_threads<false>(), smem, s>>>(d, b, step, p);
   return cudaGetLastError();
 }
 

@@ -44,10 +44,10 @@ def test_config_defaults(lib):
     assert c.max_sweeps == 30 and c.inner_max_sweeps == 30 and c.criterion == 1 and c.sort == 1
     assert c.hbm_budget_bytes == 60 << 30 and c.precision == 0
     assert c.shorten == 1 and c.fp32_params == 1 and c.inner_max_sweeps_fp32 == 1
-    assert c.fp64_gemm == 1
-    # the binding's Config mirrors the C struct: fp64_gemm is its last field
-    # (the struct is padded to 8 bytes by its uint64 member)
-    assert ctypes.sizeof(hz.Config) == (hz.Config.fp64_gemm.offset + 4 + 7) // 8 * 8
+    assert c.fp64_gemm == 1 and c.fp32_stop_permille == 50
+    # the binding's Config mirrors the C struct: fp32_stop_permille is its
+    # last field (the struct is padded to 8 bytes by its uint64 member)
+    assert ctypes.sizeof(hz.Config) == (hz.Config.fp32_stop_permille.offset + 4 + 7) // 8 * 8
 
 
 def test_strerror(lib):

@@ -185,12 +185,16 @@ def test_blocked_criterion_c2(hz):
     check(p.F, p.G, r, label="blocked C2")
 
 
+@pytest.mark.parametrize("stop", [0, 50])
 @pytest.mark.parametrize("cplx", [False, True])
-def test_mixed_precision(hz, cplx):
+def test_mixed_precision(hz, cplx, stop):
+    """stop: FP32 sweeps to their own convergence (0) or handed over to the
+    FP64 sweeps below 5 % big transformations (50, the default)."""
     p = make_pair(200, 160, 128, lo=1e-3, hi=1e3, cond=1e2, cplx=cplx, seed=21)
-    r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", block_w=16 if not cplx else 8, precision="mixed")
+    r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", block_w=16 if not cplx else 8, precision="mixed",
+                 fp32_stop_permille=stop)
     assert r.info["sweeps_fp32"] >= 1
-    check(p.F, p.G, r, label="mixed cplx=%s" % cplx)
+    check(p.F, p.G, r, label="mixed cplx=%s stop=%d" % (cplx, stop))
 
 
 @pytest.mark.parametrize("cplx", [False, True])
