@@ -5,7 +5,7 @@ sweep caps so the launch count is known in advance.
 
     python -m paper_1909_00101_gb300.profile_case [--precision mixed|fp64]
         [--m 1024] [--n 512] [--w 16] [--fp32-sweeps 2] [--fp64-sweeps 1]
-        [--shorten 0] [--fp32-params 1]
+        [--shorten 0] [--fp32-params 1] [--fp64-gemm 1]
 
 The QR shortening is off by default here, so that the Gram and apply kernels
 run on the full m-row pair.
@@ -29,6 +29,7 @@ def main():
     ap.add_argument("--fp64-sweeps", type=int, default=1)
     ap.add_argument("--shorten", type=int, default=0)
     ap.add_argument("--fp32-params", type=int, default=1)
+    ap.add_argument("--fp64-gemm", type=int, default=1)
     a = ap.parse_args()
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     sys.path.insert(0, root)
@@ -42,7 +43,7 @@ def main():
     G = torch.from_numpy(p.G).cuda()
     with hz.Solver(path="blocked", precision=a.precision, block_w=a.w, inner_max_sweeps=1,
                    fp32_max_sweeps=a.fp32_sweeps, max_sweeps=a.fp64_sweeps, shorten=a.shorten,
-                   fp32_params=a.fp32_params) as s:
+                   fp32_params=a.fp32_params, fp64_gemm=a.fp64_gemm) as s:
         r = s.solve(F, G)
     torch.cuda.synchronize()
     i = r.info
