@@ -111,6 +111,17 @@ def dist_setup(gpus):
     return None, rank, ws, local
 
 
+def whole_job_rate(total_ms: float, steps: int, dist, world: int, device="cpu"):
+    """Whole-job throughput of N replicas: the slowest rank's time (max over
+    ranks) for world x steps solves.  Returns (solves/s, max ms)."""
+    if dist is not None:
+        import torch
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * steps / (total_ms / 1e3), total_ms
+
+
 def oracle_sample(F, G, n, budget_s=10.0):
     """Time the oracle on a bounded sample of this workload's pivots and
     extrapolate: seconds per pivot (first pivots of sweep 1 of this pair) x
@@ -494,11 +505,7 @@ def main():
     clk = clocks.stop()
     step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
     total_ms = evs[0].elapsed_time(evs[-1])
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    value, total_ms = whole_job_rate(total_ms, args.steps, dist, world, dev)
 
     # accuracy of the last step: sigma against the construction, residuals
     last = infos[-1]
