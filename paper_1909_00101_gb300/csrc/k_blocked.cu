@@ -238,21 +238,19 @@ __device__ __forceinline__ void unpack_upper(int u, int& i, int& j) {
   i = u - jj * (jj + 1) / 2;
 }
 
+constexpr int INNER_THREADS = 512;  // threads of the pivot kernel
+
 // Ti: data type of the inner sweeps (double, or float in FP32 bulk sweeps);
 // To: type of the outer data (partials and Z-tilde).  P32 (FP32 bulk sweeps
 // only): the whole pivot-pair step in FP32 -- partial sums, Choleskys and
-// 2x2 parameters; its inputs are FP32 Gram partials, so FP32 arithmetic is as
-// accurate as they are.  Otherwise the sums and Choleskys are FP64.
-// Threads of the pivot kernel.
-template <bool P32>
-__host__ __device__ constexpr int inner_threads() {
-  return 512;
-}
-
+// 2x2 parameters, the latter taken by each pair's own warp; its inputs are
+// FP32 Gram partials, so FP32 arithmetic is as accurate as they are.
+// Otherwise the sums and Choleskys are FP64 and one warp (two for real
+// pivots) takes all pairs' FP64 parameters, one pair per lane.
 template <class Ti, class To, bool CPLX, int V, bool P32>
-__global__ void __launch_bounds__(inner_threads<P32>()) k_inner(BlkDims d, BlkBuffers b, int step, InnerParams prm) {
+__global__ void __launch_bounds__(INNER_THREADS) k_inner(BlkDims d, BlkBuffers b, int step, InnerParams prm) {
   constexpr int E = CPLX ? 2 : 1;
-  constexpr int NTH = inner_threads<P32>();
+  constexpr int NTH = INNER_THREADS;
   constexpr int BMAX = CPLX ? V / 2 : V;  // max columns of the pair
   using Tc = typename std::conditional<P32, float, double>::type;  // sums and Choleskys
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -967,7 +965,7 @@ cudaError_t inner_v(const BlkDims& d, const BlkBuffers& b, int step, const Inner
   auto kern = (can32 && p.par32) ? k_inner<Ti, To, CPLX, V, can32> : k_inner<Ti, To, CPLX, V, false>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  kern<<<d.nslots, (can32 && p.par32) ? inner_threads<true>() : inner_threads<false>(), smem, s>>>(d, b, step, p);
+  kern<<<d.nslots, INNER_THREADS, smem, s>>>(d, b, step, p);
   return cudaGetLastError();
 }
 
