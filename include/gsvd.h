@@ -111,6 +111,14 @@ typedef struct {
   double *sigma_f;          /* out: diag(Sigma_F), length n, sorted by descending Sigma */
   double *sigma_g;          /* out: diag(Sigma_G) */
   double *sigma;            /* out: Sigma = Sigma_F / Sigma_G */
+  void *X;                  /* optional out (NULL = not wanted): the right generalized singular vectors
+                               X = Z^-1 (n x n), real problems, gsvd_solve and gsvd_submit (Sec. 1: X may
+                               be computed from Z).  Computed from the identity X = Sigma_F U^T F +
+                               Sigma_G V^T G, which holds because [U Sigma_F; V Sigma_G] has orthonormal
+                               columns; the library keeps copies of F and G for it ((m_f + m_g) n
+                               doubles of device memory during the solve).  The GEVD of (F^T F, G^T G)
+                               is Z with Lambda = Sigma^2 */
+  int64_t ldx;
 } gsvd_problem;
 
 /* Per-solve report. */

@@ -46,7 +46,8 @@ class Problem(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int32), ("reserved", ctypes.c_int32), ("m_f", ctypes.c_int64),
                 ("m_g", ctypes.c_int64), ("n", ctypes.c_int64), ("F", ctypes.c_void_p), ("ldf", ctypes.c_int64),
                 ("G", ctypes.c_void_p), ("ldg", ctypes.c_int64), ("Z", ctypes.c_void_p), ("ldz", ctypes.c_int64),
-                ("sigma_f", ctypes.c_void_p), ("sigma_g", ctypes.c_void_p), ("sigma", ctypes.c_void_p)]
+                ("sigma_f", ctypes.c_void_p), ("sigma_g", ctypes.c_void_p), ("sigma", ctypes.c_void_p),
+                ("X", ctypes.c_void_p), ("ldx", ctypes.c_int64)]
 
 
 class Info(ctypes.Structure):
@@ -144,6 +145,7 @@ class Result:
     sigma_g: object
     sigma: object
     info: dict = field(default_factory=dict)
+    X: object = None  # right vectors X = Z^-1 when requested
 
     @property
     def status(self) -> int:
@@ -252,16 +254,27 @@ class Solver:
     def __exit__(self, *a):
         self.close()
 
-    def solve(self, F, G, *, inplace: bool = False) -> Result:
-        """GSVD of (F, G): torch CUDA tensors (device path) or numpy arrays (host path)."""
+    def solve(self, F, G, *, inplace: bool = False, right_vectors: bool = False) -> Result:
+        """GSVD of (F, G): torch CUDA tensors (device path) or numpy arrays (host
+        path).  right_vectors: also X = Z^-1 (real problems)."""
         dev, Fc, Gc, Z, sf, sg, sig = _prepare(F, G, inplace)
         p = _problem(Fc, Gc, Z, sf, sg, sig, dev)
+        X = None
+        if right_vectors:
+            n = Z.shape[0]
+            if dev:
+                import torch
+                X = torch.empty((n, n), dtype=Z.dtype, device=Z.device).t()
+                p.X, p.ldx = X.data_ptr(), _ld(X, True)
+            else:
+                X = np.zeros((n, n), dtype=Z.dtype, order="F")
+                p.X, p.ldx = X.ctypes.data, _ld(X, False)
         info = Info()
         if dev:
             import torch
             torch.cuda.current_stream().synchronize()
         self._lib.gsvd_solve(self._h, ctypes.byref(p), ctypes.byref(info))
-        return Result(Fc, Gc, Z, sf, sg, sig, info.as_dict())
+        return Result(Fc, Gc, Z, sf, sg, sig, info.as_dict(), X)
 
     def solve_problems(self, probs) -> list:
         """Raw batched call on prepared Problem structs; returns the Info dicts."""
@@ -330,7 +343,7 @@ def solve_small_noalloc(pairs, *, stream=None, **cfg) -> tuple:
     return st, res
 
 
-def solve(F, G, *, inplace: bool = False, **cfg) -> Result:
+def solve(F, G, *, inplace: bool = False, right_vectors: bool = False, **cfg) -> Result:
     """One-shot GSVD (creates and destroys a handle)."""
     with Solver(**cfg) as s:
-        return s.solve(F, G, inplace=inplace)
+        return s.solve(F, G, inplace=inplace, right_vectors=right_vectors)

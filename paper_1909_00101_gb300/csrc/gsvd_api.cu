@@ -220,6 +220,7 @@ int validate(const gsvd_problem* p) {
   if (p->n > 32768 || p->m_f > (int64_t)1 << 30 || p->m_g > (int64_t)1 << 30) return GSVD_EINVAL;
   if (p->ldf < p->m_f || p->ldg < p->m_g || p->ldz < p->n) return GSVD_EINVAL;
   if (!p->F || !p->G || !p->Z || !p->sigma_f || !p->sigma_g || !p->sigma) return GSVD_EINVAL;
+  if (p->X && (p->dtype != GSVD_R64 || p->ldx < p->n)) return GSVD_EINVAL;
   return GSVD_OK;
 }
 
@@ -654,8 +655,8 @@ int solve_shortened(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* in
   return st;
 }
 
-int solve_device(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info, DevBuf& ws,
-                 unsigned long long* h_ctr, cudaStream_t s) {
+int solve_device_core(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info, DevBuf& ws,
+                      unsigned long long* h_ctr, cudaStream_t s) {
   Plan P;
   if (!make_plan(cfg, p->dtype, p->m_f, p->m_g, p->n, P)) return GSVD_EINVAL;
   if (shorten_applies(cfg, P, p->m_f, p->m_g, p->n)) {
@@ -672,6 +673,31 @@ int solve_device(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info,
   return solve_plain(cfg, p, info, ws, h_ctr, s);
 }
 
+// one problem with device pointers; with p->X also the right vectors
+// X = Z^-1 = Sigma_F U^T F + Sigma_G V^T G (the columns of [U Sigma_F;
+// V Sigma_G] are orthonormal, so it is the left inverse of Z applied to
+// [F; G] = [U Sigma_F; V Sigma_G] Z^-1), from copies of the inputs
+int solve_device(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info, DevBuf& ws,
+                 unsigned long long* h_ctr, cudaStream_t s) {
+  if (!p->X) return solve_device_core(cfg, p, info, ws, h_ctr, s);
+  const int n = (int)p->n, mf = (int)p->m_f, mg = (int)p->m_g;
+  DevBuf keep;
+  CK(keep.ensure(sizeof(double) * (((size_t)mf + mg) * n + (size_t)n * n) + 256));
+  double* F0 = static_cast<double*>(keep.p);
+  double* G0 = F0 + (size_t)mf * n;
+  double* T = G0 + (size_t)mg * n;
+  CK(cudaMemcpy2DAsync(F0, (size_t)mf * 8, p->F, p->ldf * 8, (size_t)mf * 8, n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpy2DAsync(G0, (size_t)mg * 8, p->G, p->ldg * 8, (size_t)mg * 8, n, cudaMemcpyDeviceToDevice, s));
+  const int st = solve_device_core(cfg, p, info, ws, h_ctr, s);
+  if (st != GSVD_OK && st != GSVD_ENOCONV) return st;
+  double* X = static_cast<double*>(p->X);
+  CK(dgemm(true, false, n, n, mf, 1.0, (const double*)p->F, p->ldf, F0, mf, 0.0, X, p->ldx, 0, s));
+  CK(dgemm(true, false, n, n, mg, 1.0, (const double*)p->G, p->ldg, G0, mg, 0.0, T, n, 0, s));
+  CK(launch_rows_combine(n, X, p->ldx, p->sigma_f, T, n, p->sigma_g, s));
+  CK(cudaStreamSynchronize(s));
+  return st;
+}
+
 // host pointers: stage through device buffers (pinned or pageable host memory)
 int solve_host(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info, DevBuf& ws, unsigned long long* h_ctr,
                cudaStream_t s) {
@@ -680,7 +706,8 @@ int solve_host(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info, D
   const size_t bF = align256((size_t)p->m_f * p->n * es), bG = align256((size_t)p->m_g * p->n * es),
                bZ = align256((size_t)p->n * p->n * es), bv = align256((size_t)p->n * 8);
   DevBuf stage;
-  CK(stage.ensure(bF + bG + bZ + 3 * bv));
+  const size_t bX = p->X ? align256((size_t)p->n * p->n * es) : 0;
+  CK(stage.ensure(bF + bG + bZ + 3 * bv + bX));
   unsigned char* b = static_cast<unsigned char*>(stage.p);
   gsvd_problem d = *p;
   d.F = b; d.ldf = p->m_f;
@@ -689,6 +716,10 @@ int solve_host(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info, D
   d.sigma_f = reinterpret_cast<double*>(b + bF + bG + bZ);
   d.sigma_g = reinterpret_cast<double*>(b + bF + bG + bZ + bv);
   d.sigma = reinterpret_cast<double*>(b + bF + bG + bZ + 2 * bv);
+  if (p->X) {
+    d.X = b + bF + bG + bZ + 3 * bv;
+    d.ldx = p->n;
+  }
   CK(cudaMemcpy2DAsync(d.F, p->m_f * es, p->F, p->ldf * es, p->m_f * es, p->n, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpy2DAsync(d.G, p->m_g * es, p->G, p->ldg * es, p->m_g * es, p->n, cudaMemcpyHostToDevice, s));
   int st = solve_device(cfg, &d, info, ws, h_ctr, s);
@@ -699,6 +730,8 @@ int solve_host(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info, D
   CK(cudaMemcpyAsync(p->sigma_f, d.sigma_f, p->n * 8, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(p->sigma_g, d.sigma_g, p->n * 8, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(p->sigma, d.sigma, p->n * 8, cudaMemcpyDeviceToHost, s));
+  if (p->X)
+    CK(cudaMemcpy2DAsync(p->X, p->ldx * es, d.X, p->n * es, p->n * es, p->n, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   return st;
 }
@@ -711,7 +744,8 @@ int solve_any(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info, De
     return v;
   }
   const bool dev = is_device_ptr(p->F);
-  if (dev != is_device_ptr(p->G) || dev != is_device_ptr(p->Z) || dev != is_device_ptr(p->sigma)) {
+  if (dev != is_device_ptr(p->G) || dev != is_device_ptr(p->Z) || dev != is_device_ptr(p->sigma) ||
+      (p->X && dev != is_device_ptr(p->X))) {
     info->status = GSVD_EINVAL;
     return GSVD_EINVAL;
   }
@@ -853,6 +887,7 @@ int gsvd_solve_batched(gsvd_handle h, const gsvd_problem* ps, int32_t count, gsv
     int v = validate(&ps[k]);
     if (v == GSVD_OK && !(is_device_ptr(ps[k].F) && is_device_ptr(ps[k].G) && is_device_ptr(ps[k].Z)))
       v = GSVD_EINVAL;
+    if (v == GSVD_OK && ps[k].X) v = GSVD_EINVAL;  // right vectors: gsvd_solve and gsvd_submit only
     if (v != GSVD_OK) {
       loc[k].status = v;
       continue;

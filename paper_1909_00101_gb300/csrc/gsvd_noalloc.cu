@@ -65,7 +65,7 @@ extern "C" int gsvd_solve_small_noalloc(const gsvd_problem* ps, int32_t count, c
     const gsvd_problem& p = ps[k];
     if ((p.dtype != GSVD_R64 && p.dtype != GSVD_C128) || p.n < 1 || p.m_f < p.n || p.m_g < p.n ||
         p.ldf < p.m_f || p.ldg < p.m_g || p.ldz < p.n || !p.F || !p.G || !p.Z || !p.sigma_f || !p.sigma_g ||
-        !p.sigma)
+        !p.sigma || p.X)
       return GSVD_EINVAL;
     if (p.n > 64) return GSVD_ETOOBIG;
     if (!on_device(p.F) || !on_device(p.G) || !on_device(p.Z) || !on_device(p.sigma_f) ||

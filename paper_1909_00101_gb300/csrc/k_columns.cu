@@ -336,6 +336,21 @@ cudaError_t launch_gemm_f64_by_f32(int m, int n, bool cplx, const double* A, lon
   return cudaGetLastError();
 }
 
+// X(i, j) <- sf_i X(i, j) + sg_i T(i, j)  (n x n, column-major)
+__global__ void k_rows_combine(int n, double* X, long long ldx, const double* sf, const double* T, long long ldt,
+                               const double* sg) {
+  const int j = blockIdx.y;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    X[(size_t)j * ldx + i] = fma(sf[i], X[(size_t)j * ldx + i], sg[i] * T[(size_t)j * ldt + i]);
+}
+
+cudaError_t launch_rows_combine(int n, double* X, long long ldx, const double* sf, const double* T, long long ldt,
+                                const double* sg, cudaStream_t s) {
+  dim3 grid((n + 255) / 256, n);
+  k_rows_combine<<<grid, 256, 0, s>>>(n, X, ldx, sf, T, ldt, sg);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rowscale(int n, bool cplx, const double* zdiag, const float* Z32, long long ld32, double* Z,
                             long long ldz, cudaStream_t s) {
   const int E = cplx ? 2 : 1;

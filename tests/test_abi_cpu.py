@@ -80,6 +80,12 @@ def test_invalid_problems_rejected_before_any_launch(lib):
     assert lib.gsvd_solve(h, ctypes.byref(p), ctypes.byref(info)) == hz.EINVAL
     p.n = 4
     assert lib.gsvd_solve_batched(h, None, -1, None) == hz.EINVAL
+    # right vectors: real problems only, ld >= n
+    X = np.zeros((4, 4), order="F")
+    p.X, p.ldx = X.ctypes.data, 3
+    assert lib.gsvd_solve(h, ctypes.byref(p), ctypes.byref(info)) == hz.EINVAL
+    p.ldx, p.dtype = 4, 1
+    assert lib.gsvd_solve(h, ctypes.byref(p), ctypes.byref(info)) == hz.EINVAL
     assert lib.gsvd_destroy(h) == 0
 
 

@@ -210,6 +210,52 @@ def test_mixed_fp32_parameters(hz, cplx, fp32_params):
     check(p.F, p.G, r, label="mixed fp32_params=%d cplx=%s" % (fp32_params, cplx))
 
 
+# ------------------------------------------------------- right vectors ----
+
+@pytest.mark.parametrize("kw,shape", [(dict(path="pointwise"), (64, 48, 32)),
+                                      (dict(path="blocked", block_w=8, shorten=0), (150, 130, 96)),
+                                      (dict(path="blocked", block_w=8), (400, 300, 96)),
+                                      (dict(path="blocked", block_w=16, precision="mixed"), (300, 260, 128))])
+def test_right_vectors(hz, kw, shape):
+    """X = Z^-1 (Sec. 1): X Z = I to working accuracy relative to ||X|| ||Z||,
+    and X equals the inverse of the returned Z."""
+    mf, mg, n = shape
+    p = make_pair(mf, mg, n, lo=1e-3, hi=1e3, cond=1e2, seed=n + 3)
+    r = hz.solve(_dev(p.F), _dev(p.G), right_vectors=True, **kw)
+    assert r.status == 0, r.info
+    X, Z = _np(r.X), _np(r.Z)
+    eye = np.eye(n)
+    err = np.max(np.abs(X @ Z - eye)) / (np.linalg.norm(X, 2) * np.linalg.norm(Z, 2))
+    assert err <= 64 * n * 2.0 ** -53, err
+    Zi = np.linalg.inv(Z)
+    assert np.max(np.abs(X - Zi)) / np.max(np.abs(Zi)) <= 1e-9
+    check(p.F, p.G, r, label="right vectors %s" % (kw,))
+
+
+def test_right_vectors_not_in_batched_calls(hz):
+    """Batched calls reject a problem that asks for X (per-problem status)."""
+    import ctypes
+    p = make_pair(100, 90, 72, seed=6)
+    F, G = _dev(p.F), _dev(p.G)
+    Z = torch.empty((72, 72), dtype=torch.float64, device="cuda").t()
+    X = torch.empty((72, 72), dtype=torch.float64, device="cuda").t()
+    v = [torch.empty(72, dtype=torch.float64, device="cuda") for _ in range(3)]
+    prob = hz._problem(F, G, Z, v[0], v[1], v[2], True)
+    prob.X, prob.ldx = X.data_ptr(), 72
+    infos = (hz.Info * 1)()
+    with hz.Solver() as s:
+        torch.cuda.synchronize()
+        st = s._lib.gsvd_solve_batched(s._h, ctypes.byref(prob), 1, infos)
+    assert st == hz.EINVAL and infos[0].status == hz.EINVAL
+
+
+def test_right_vectors_host_path(hz):
+    p = make_pair(100, 90, 72, seed=6)
+    d = hz.solve(_dev(p.F), _dev(p.G), path="blocked", block_w=8, right_vectors=True)
+    h = hz.solve(p.F.copy(order="F"), p.G.copy(order="F"), path="blocked", block_w=8, right_vectors=True)
+    assert np.array_equal(_np(d.X), h.X)
+
+
 # ------------------------------------------------------- reproducibility ----
 
 @pytest.mark.parametrize("kw", [dict(path="pointwise"), dict(path="blocked", block_w=16),
