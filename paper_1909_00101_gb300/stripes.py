@@ -1,0 +1,225 @@
+"""Multi-GPU stripe algorithm of Sec. 4: host-side schedule, exchange map and
+driver.
+
+The columns of F, G and Z are cut into ns = 2 s stripes of equal width (s
+processes, one per GPU).  In each outer step every process holds two stripes,
+runs the single-GPU algorithm on that pair (the pair is a GSVD problem of its
+own: any nonsingular transformation Z_pq that it returns is applied to the
+pair's columns of F, G and Z), and then sends each of its two transformed
+stripes to the process that holds that stripe in the next step, as its first
+or second stripe.  The steps of a sweep follow the round-robin ordering of the
+ns stripes (every pair of stripes meets once per sweep); a sweep ends with one
+sum-reduction of the big-transformation counters, and the algorithm stops
+after a sweep without big transformations (Sec. 4.2, Sec. 2.5).
+
+The exchange map follows Sec. 4.1.3: for step k and process r it gives the
+pair (p, q) the process holds and, for each of its two stripes, the target
+process encoded as -(t + 1) when the stripe becomes the target's first stripe
+and t + 1 when it becomes the second.
+
+This module is host logic only (no arithmetic of the method): the pair solver
+is passed in.  On GPUs it is the library's own solve of the pair; the tests
+run it on CPU ranks (gloo).  Any process that fails ends the others' waits by
+a timeout, which the driver reports as a status instead of hanging.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from datetime import timedelta
+
+import numpy as np
+
+
+def round_robin(ns: int) -> list:
+    """Round-robin ("circle method") ordering of ns (even) stripes: ns - 1
+    steps of ns / 2 disjoint pairs (p, q), p < q; stripe ns - 1 stays, the
+    others rotate.  Every pair of stripes occurs in exactly one step."""
+    if ns < 2 or ns % 2:
+        raise ValueError("need an even number of stripes >= 2")
+    steps = []
+    for s in range(ns - 1):
+        pairs = []
+        for k in range(ns // 2):
+            if k == 0:
+                a, b = ns - 1, s
+            else:
+                a, b = (s + k) % (ns - 1), (s - k + (ns - 1)) % (ns - 1)
+            pairs.append((min(a, b), max(a, b)))
+        steps.append(pairs)
+    return steps
+
+
+@dataclass(frozen=True)
+class StepMap:
+    p: int    # global index of the first local stripe
+    q: int    # global index of the second local stripe
+    t0: int   # target of the first stripe: -(t + 1) as the target's first stripe, t + 1 as its second
+    t1: int   # target of the second stripe, encoded alike
+
+
+def exchange_map(s: int) -> list:
+    """The map (k, r) -> (p, q, t0, t1) of Sec. 4.1.3 for s processes and 2 s
+    stripes: [k][r] for the ns - 1 steps of a sweep.  The step after the last
+    one is step 0 of the next sweep."""
+    ns = 2 * s
+    steps = round_robin(ns)
+    holder = []
+    for pairs in steps:
+        h = {}
+        for r, (p, q) in enumerate(pairs):
+            h[p] = (r, 0)
+            h[q] = (r, 1)
+        holder.append(h)
+    out = []
+    for k, pairs in enumerate(steps):
+        nxt = holder[(k + 1) % len(steps)]
+        row = []
+        for r, (p, q) in enumerate(pairs):
+            codes = []
+            for stripe in (p, q):
+                t, slot = nxt[stripe]
+                codes.append(-(t + 1) if slot == 0 else t + 1)
+            row.append(StepMap(p, q, codes[0], codes[1]))
+        out.append(row)
+    return out
+
+
+def decode(code: int) -> tuple:
+    """(target process, slot 0 or 1) of an encoded target."""
+    return (-code - 1, 0) if code < 0 else (code - 1, 1)
+
+
+def senders(maps: list, k: int, r: int) -> tuple:
+    """(process, its local stripe 0 or 1) that sends this process's slot 0 and
+    slot 1 stripes after step k."""
+    src = [None, None]
+    for rr, m in enumerate(maps[k]):
+        for local, code in enumerate((m.t0, m.t1)):
+            t, slot = decode(code)
+            if t == r:
+                src[slot] = (rr, local)
+    return src[0], src[1]
+
+
+@dataclass
+class StripeResult:
+    status: int            # 0 ok, -3 no convergence in max_sweeps, -6 a wait timed out (another process failed)
+    sweeps: int
+    p: int                 # global stripe indices held at the end (first, second)
+    q: int
+    F: np.ndarray          # the two stripes of F, G, Z after the sweeps (not normalised)
+    G: np.ndarray
+    Z: np.ndarray
+
+
+def prescale_stripes(F: np.ndarray, G: np.ndarray, p: int, q: int, w: int, n: int) -> tuple:
+    """Sec. 3.3 prescaling of two stripes (global stripes p and q of width w):
+    z_j = 1 / ||g_j||, f_j *= z_j, g_j *= z_j, and Z0's columns for them
+    (n x 2w, z_j in the global row of column j)."""
+    s = np.sqrt(np.sum(G * G, axis=0))
+    if np.any(s == 0.0) or not np.all(np.isfinite(s)):
+        raise ValueError("G is rank deficient")
+    z = 1.0 / s
+    Z0 = np.zeros((n, 2 * w))
+    cols = list(range(p * w, p * w + w)) + list(range(q * w, q * w + w))
+    for j, c in enumerate(cols):
+        Z0[c, j] = z[j]
+    return F * z[None, :], G * z[None, :], Z0
+
+
+def _run(F, G, Z, *, rank, world, dist, solve_pair, max_sweeps=30, timeout_s=30.0) -> StripeResult:
+    import torch
+    maps = exchange_map(world)
+    nsteps = len(maps)
+    w = F.shape[1] // 2
+    mf, mg, n = F.shape[0], G.shape[0], Z.shape[0]
+    rows = mf + mg + n
+    tmo = timedelta(seconds=timeout_s)
+    # the pair's columns of F, G and Z stacked (rows x 2w), one buffer
+    buf = np.concatenate([F, G, Z], axis=0)
+    sweeps = 0
+    for sweep in range(max_sweeps):
+        big = 0
+        for k in range(nsteps):
+            m = maps[k][rank]
+            Fpq, Gpq = buf[:mf], buf[mf:mf + mg]
+            Zpq, b = solve_pair(np.ascontiguousarray(Fpq), np.ascontiguousarray(Gpq))
+            buf = buf @ Zpq
+            big += int(b)
+            # exchange: each local stripe to its holder in the next step
+            out = [torch.from_numpy(np.ascontiguousarray(buf[:, :w])),
+                   torch.from_numpy(np.ascontiguousarray(buf[:, w:]))]
+            inc = [torch.empty((rows, w), dtype=torch.float64) for _ in range(2)]
+            src = senders(maps, k, rank)
+            works = []
+            local_copy = {}
+            for slot in (0, 1):
+                sr, sl = src[slot]
+                if sr == rank:
+                    local_copy[slot] = sl
+                else:
+                    works.append(dist.irecv(inc[slot], src=sr, tag=slot + 1))
+            for local, code in enumerate((m.t0, m.t1)):
+                t, slot = decode(code)
+                if t != rank:
+                    works.append(dist.isend(out[local], dst=t, tag=slot + 1))
+            for slot, sl in local_copy.items():
+                inc[slot].copy_(out[sl])
+            try:
+                for wk in works:
+                    wk.wait(tmo)
+            except RuntimeError:
+                return StripeResult(-6, sweeps, m.p, m.q, buf[:mf], buf[mf:mf + mg], buf[mf + mg:])
+            buf = np.concatenate([inc[0].numpy(), inc[1].numpy()], axis=1)
+        sweeps += 1
+        tot = torch.tensor([big], dtype=torch.int64)
+        try:
+            if world > 1:
+                dist.all_reduce(tot, async_op=True).wait(tmo)
+        except RuntimeError:
+            m = maps[0][rank]
+            return StripeResult(-6, sweeps, m.p, m.q, buf[:mf], buf[mf:mf + mg], buf[mf + mg:])
+        if int(tot.item()) == 0:
+            m = maps[0][rank]
+            return StripeResult(0, sweeps, m.p, m.q, buf[:mf], buf[mf:mf + mg], buf[mf + mg:])
+    m = maps[0][rank]
+    return StripeResult(-3, sweeps, m.p, m.q, buf[:mf], buf[mf:mf + mg], buf[mf + mg:])
+
+
+def run(F, G, Z, *, rank, world, dist, solve_pair, max_sweeps: int = 30, timeout_s: float = 30.0) -> StripeResult:
+    """The sweeps of Sec. 4.2 for this process.
+
+    F (m_F x 2w), G (m_G x 2w), Z (n x 2w): this process's two stripes of
+    step 0 (its pair in exchange_map(world)[0][rank]), prescaled
+    (prescale_stripes).  solve_pair(Fpq, Gpq) -> (Zpq, big): a nonsingular
+    transformation of the pair and its count of big transformations.  dist:
+    torch.distributed with an initialised process group.  A wait that runs
+    out of time (a failed peer) gives status -6; no convergence in
+    max_sweeps gives -3.  At the end every process holds the stripes of step
+    0 again (the map wraps around after each sweep).
+    """
+    return _run(F, G, Z, rank=rank, world=world, dist=dist, solve_pair=solve_pair, max_sweeps=max_sweeps,
+                timeout_s=timeout_s)
+
+
+def library_pair_solver(solver):
+    """solve_pair for run() on a GPU process: the library's solve of the pair
+    (host arrays in, through the C ABI; the pair's Z and its count of big
+    transformations out).  solver: a paper_1909_00101_gb300.Solver."""
+    def solve_pair(Fp, Gp):
+        r = solver.solve(np.asfortranarray(Fp), np.asfortranarray(Gp))
+        if r.status not in (0, -3):
+            raise RuntimeError("pair solve failed: status %d" % r.status)
+        return np.asarray(r.Z), int(r.info["transf_big"])
+    return solve_pair
+
+
+def finalize(F: np.ndarray, G: np.ndarray, Z: np.ndarray) -> dict:
+    """Sec. 3.4 for a process's columns: Sigma_F = ||f_j||, Sigma_G = ||g_j||,
+    Theta_j = (Sigma_F^2 + Sigma_G^2)^(-1/2), U = F / ||f||, V = G / ||g||,
+    Z Theta, and Sigma = ||f_j|| / ||g_j|| (not sorted)."""
+    sf = np.sqrt(np.sum(F * F, axis=0))
+    sg = np.sqrt(np.sum(G * G, axis=0))
+    th = 1.0 / np.sqrt(sf * sf + sg * sg)
+    return {"U": F / sf[None, :], "V": G / sg[None, :], "Z": Z * th[None, :], "sigma_f": sf * th,
+            "sigma_g": sg * th, "sigma": sf / sg}

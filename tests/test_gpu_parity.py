@@ -256,6 +256,23 @@ def test_right_vectors_host_path(hz):
     assert np.array_equal(_np(d.X), h.X)
 
 
+# ------------------------------------------------------ stripe driver ----
+
+def test_stripe_driver_with_the_library_pair_solver(hz):
+    """Sec. 4 driver on one process (two stripes, no exchange partner) with the
+    library solving the pair: the same GSVD as the oracle."""
+    from paper_1909_00101_gb300 import stripes as S
+    p = make_pair(40, 36, 16, lo=1e-2, hi=1e2, cond=10.0, seed=7)
+    w = 8
+    Fl, Gl, Zl = S.prescale_stripes(p.F, p.G, 0, 1, w, 16)
+    with hz.Solver(path="blocked", block_w=4) as s:
+        res = S.run(Fl, Gl, Zl, rank=0, world=1, dist=None, solve_pair=S.library_pair_solver(s))
+    assert res.status == 0, res
+    fin = S.finalize(res.F, res.G, res.Z)
+    ref = oracle.gsvd(p.F, p.G)
+    assert rel_sigma_err(np.sort(fin["sigma"])[::-1], ref["sigma"]) <= 1e-12
+
+
 # ------------------------------------------------------- reproducibility ----
 
 @pytest.mark.parametrize("kw", [dict(path="pointwise"), dict(path="blocked", block_w=16),

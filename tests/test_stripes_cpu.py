@@ -1,0 +1,125 @@
+"""The multi-GPU stripe algorithm of Sec. 4 on CPU ranks (gloo): the
+exchange map, a full distributed solve against the oracle, and a failed rank
+that the others detect on the host by a timeout instead of hanging."""
+import multiprocessing as pymp
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1909_00101_gb300 import stripes as S  # noqa: E402
+
+
+def _port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+@pytest.mark.parametrize("s", [1, 2, 3, 4, 6])
+def test_exchange_map_is_a_round_robin_with_consistent_targets(s):
+    ns = 2 * s
+    maps = S.exchange_map(s)
+    assert len(maps) == ns - 1
+    met = set()
+    for k, row in enumerate(maps):
+        held = [x for m in row for x in (m.p, m.q)]
+        assert sorted(held) == list(range(ns))          # disjoint pairs covering every stripe
+        for m in row:
+            assert m.p < m.q and (m.p, m.q) not in met
+            met.add((m.p, m.q))
+        # targets: where each stripe is held in the next step (first or second)
+        nxt = maps[(k + 1) % len(maps)]
+        slots = {}
+        for r, m in enumerate(row):
+            for stripe, code in ((m.p, m.t0), (m.q, m.t1)):
+                t, slot = S.decode(code)
+                assert (code < 0) == (slot == 0)
+                assert (nxt[t].p if slot == 0 else nxt[t].q) == stripe
+                slots[(t, slot)] = slots.get((t, slot), 0) + 1
+        assert all(v == 1 for v in slots.values()) and len(slots) == ns
+        for r in range(s):
+            src0, src1 = S.senders(maps, k, r)
+            assert src0 is not None and src1 is not None
+    assert len(met) == ns * (ns - 1) // 2                # every pair once per sweep
+
+
+def _solve_pair(Fp, Gp):
+    import oracle
+    r = oracle.gsvd(Fp, Gp)
+    assert r["status"] == 0
+    return r["Z"], r["transf_big"]
+
+
+def _rank_main(rank, world, port, out, F, G, w, fail_rank):
+    import torch.distributed as dist
+    from datetime import timedelta
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=world,
+                            timeout=timedelta(seconds=20))
+    try:
+        if rank == fail_rank:
+            raise SystemExit(3)  # this rank fails before its first step
+        m = S.exchange_map(world)[0][rank]
+        cols = list(range(m.p * w, m.p * w + w)) + list(range(m.q * w, m.q * w + w))
+        Fl, Gl, Zl = S.prescale_stripes(F[:, cols], G[:, cols], m.p, m.q, w, F.shape[1])
+        res = S.run(Fl, Gl, Zl, rank=rank, world=world, dist=dist, solve_pair=_solve_pair, max_sweeps=20,
+                    timeout_s=3.0 if fail_rank >= 0 else 30.0)
+        fin = S.finalize(res.F, res.G, res.Z)
+        np.savez(os.path.join(out, "r%d.npz" % rank), status=res.status, sweeps=res.sweeps, p=res.p, q=res.q, **fin)
+    finally:
+        if rank != fail_rank:
+            dist.destroy_process_group()
+
+
+def _spawn(world, F, G, w, out, fail_rank=-1):
+    ctx = pymp.get_context("spawn")
+    port = _port()
+    ps = [ctx.Process(target=_rank_main, args=(r, world, port, out, F, G, w, fail_rank)) for r in range(world)]
+    for p in ps:
+        p.start()
+    for p in ps:
+        p.join(120)
+    return [p.exitcode for p in ps]
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_ranks_match_the_oracle(tmp_path, world):
+    import oracle
+    from paper_1909_00101_gb300.inputs import make_pair
+    w = 4
+    n = 2 * world * w
+    p = make_pair(40, 36, n, lo=1e-2, hi=1e2, cond=10.0, seed=5)
+    codes = _spawn(world, p.F, p.G, w, str(tmp_path))
+    assert codes == [0] * world
+    U = np.zeros_like(p.F)
+    Z = np.zeros((n, n))
+    sf = np.zeros(n)
+    sig = np.zeros(n)
+    for r in range(world):
+        d = np.load(tmp_path / ("r%d.npz" % r))
+        assert int(d["status"]) == 0
+        for slot, stripe in ((0, int(d["p"])), (1, int(d["q"]))):
+            c = slice(stripe * w, stripe * w + w)
+            loc = slice(slot * w, slot * w + w)
+            U[:, c] = d["U"][:, loc]
+            Z[:, c] = d["Z"][:, loc]
+            sf[c] = d["sigma_f"][loc]
+            sig[c] = d["sigma"][loc]
+    ref = oracle.gsvd(p.F, p.G)
+    got = np.sort(sig)[::-1]
+    assert np.max(np.abs(got - ref["sigma"]) / ref["sigma"]) <= 1e-12
+    assert np.linalg.norm(U.T @ U - np.eye(n)) <= 1e-12 * n
+    assert np.linalg.norm(p.F @ Z - U * sf[None, :]) / np.linalg.norm(p.F) <= 1e-13 * n
+
+
+def test_a_failed_rank_ends_the_others_waits(tmp_path):
+    from paper_1909_00101_gb300.inputs import make_pair
+    world, w = 2, 4
+    p = make_pair(40, 36, 2 * world * w, seed=6)
+    codes = _spawn(world, p.F, p.G, w, str(tmp_path), fail_rank=1)
+    assert codes[1] != 0 and codes[0] == 0
+    d = np.load(tmp_path / "r0.npz")
+    assert int(d["status"]) == -6
