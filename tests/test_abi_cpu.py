@@ -122,3 +122,29 @@ def test_workspace_bytes_grows_with_size(lib):
     assert planes <= got_oz - got <= planes + 65536  # + the per-row scale exponents
     # complex problems are not shortened
     assert lib.gsvd_workspace_bytes(ctypes.byref(sh), 1, m, m, n) == c
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Sizes and field offsets of gsvd_config, gsvd_problem and gsvd_info as
+    compiled from include/gsvd.h equal the ctypes mirrors of the binding."""
+    import shutil
+    import subprocess
+    import paper_1909_00101_gb300 as hz
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gsvd.h"', "int main(void) {"]
+    checks = []
+    for cname, cls in (("gsvd_config", hz.Config), ("gsvd_problem", hz.Problem), ("gsvd_info", hz.Info)):
+        lines.append('  printf("%%zu\\n", sizeof(%s));' % cname)
+        checks.append(ctypes.sizeof(cls))
+        for fname, _ in cls._fields_:
+            lines.append('  printf("%%zu\\n", offsetof(%s, %s));' % (cname, fname))
+            checks.append(getattr(cls, fname).offset)
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "abi.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "abi"
+    subprocess.check_call(["gcc", "-I", os.path.join(root, "include"), "-o", str(exe), str(src)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    assert got == checks
