@@ -41,7 +41,7 @@ __device__ __forceinline__ T warp_sum(T v) {
 template <class T>
 __device__ __forceinline__ void warp_sum4(T v[4]) {
   const int lane = threadIdx.x & 31;
-  // round 1 (offset 16): lanes < 16 keep (v0, v1), lanes >= 16 keep (v2, v3)
+  // stage 1 (offset 16): lanes < 16 keep (v0, v1), lanes >= 16 keep (v2, v3)
   const bool hi16 = lane & 16;
   T s0 = hi16 ? v[0] : v[2];
   T s1 = hi16 ? v[1] : v[3];
@@ -51,13 +51,13 @@ __device__ __forceinline__ void warp_sum4(T v[4]) {
   T k1 = hi16 ? v[3] : v[1];
   k0 += r0;
   k1 += r1;
-  // round 2 (offset 8): keep one of the two
+  // stage 2 (offset 8): keep one of the two
   const bool hi8 = lane & 8;
   T s = hi8 ? k0 : k1;
   T r = __shfl_xor_sync(FULL, s, 8);
   T k = hi8 ? k1 : k0;
   k += r;
-  // rounds 3..5: plain butterfly within groups of 8
+  // stages 3..5: plain butterfly within groups of 8
   k += __shfl_xor_sync(FULL, k, 4);
   k += __shfl_xor_sync(FULL, k, 2);
   k += __shfl_xor_sync(FULL, k, 1);
