@@ -181,6 +181,19 @@ int gsvd_submit(gsvd_handle h, const gsvd_problem *p, uint64_t *ticket);
  * request's final status (info filled, the ticket released). */
 int gsvd_poll(gsvd_handle h, uint64_t ticket, gsvd_info *info);
 
+/* Block-width autotuner: times one sweep of each candidate block width (real
+ * 8, 16, 32; complex 4, 8, 16; widths with 2w > n are skipped) on a synthetic
+ * pair of this shape (deterministic values in [-1, 1)) with the handle's
+ * configuration, and records the fastest for the problem's class (data type,
+ * precision, shortened or not, n rounded up to a power of two).  Later solves
+ * of that class through this handle (gsvd_solve, gsvd_solve_batched,
+ * gsvd_submit) use the recorded width when the configuration's block_w is 0.
+ * *block_w receives the width, or 0 when there is nothing to choose (the
+ * class runs on the pointwise kernel, or the configuration fixes block_w).
+ * Blocks until done; allocates the synthetic pair for the duration of the
+ * call. */
+int gsvd_autotune(gsvd_handle h, int32_t dtype, int64_t m_f, int64_t m_g, int64_t n, int32_t *block_w);
+
 /* Device bytes a solve of this shape needs beyond the caller's buffers. */
 uint64_t gsvd_workspace_bytes(const gsvd_config *cfg, int32_t dtype, int64_t m_f, int64_t m_g, int64_t n);
 

@@ -276,6 +276,17 @@ class Solver:
         self._lib.gsvd_solve(self._h, ctypes.byref(p), ctypes.byref(info))
         return Result(Fc, Gc, Z, sf, sg, sig, info.as_dict(), X)
 
+    def autotune(self, m_f: int, m_g: int, n: int, cplx: bool = False) -> int:
+        """gsvd_autotune: time the candidate block widths for this shape on a
+        synthetic pair and record the fastest for later solves of its class;
+        returns the width (0: nothing to choose)."""
+        w = ctypes.c_int32(0)
+        st = self._lib.gsvd_autotune(self._h, C128 if cplx else R64, ctypes.c_int64(m_f), ctypes.c_int64(m_g),
+                                     ctypes.c_int64(n), ctypes.byref(w))
+        if st != 0:
+            raise RuntimeError("gsvd_autotune: %s" % strerror(st))
+        return int(w.value)
+
     def solve_problems(self, probs) -> list:
         """Raw batched call on prepared Problem structs; returns the Info dicts."""
         arr = (Problem * len(probs))(*probs)

@@ -249,7 +249,37 @@ struct gsvd_ctx {
   int inflight = 0;
   bool stop = false;
   std::vector<std::thread> workers;
+  // autotuned block widths by problem class (gsvd_autotune)
+  std::mutex tune_mu;
+  std::map<uint32_t, int> tuned;
 };
+
+namespace {
+
+// problem class of the autotuner: data type, precision, whether the pair is
+// shortened, and n rounded up to a power of two
+uint32_t tune_key(const gsvd_config& cfg, int dtype, int64_t mf, int64_t mg, int64_t n) {
+  int lg = 0;
+  while (((int64_t)1 << lg) < n && lg < 31) ++lg;
+  const bool sh = dtype == GSVD_R64 &&
+                  (cfg.shorten == 2 || (cfg.shorten == 1 && (double)(mf + mg) >= 2.6 * (double)n));
+  return (uint32_t)lg | ((uint32_t)(dtype == GSVD_C128) << 8) | ((uint32_t)(cfg.precision == GSVD_PREC_MIXED) << 9) |
+         ((uint32_t)sh << 10);
+}
+
+// the handle's configuration for one problem: the autotuned block width of
+// its class when the configuration leaves the width open
+gsvd_config cfg_for(gsvd_ctx* h, const gsvd_problem* p) {
+  gsvd_config c = h->cfg;
+  if (c.block_w == 0) {
+    std::lock_guard<std::mutex> lk(h->tune_mu);
+    auto it = h->tuned.find(tune_key(c, p->dtype, p->m_f, p->m_g, p->n));
+    if (it != h->tuned.end()) c.block_w = it->second;
+  }
+  return c;
+}
+
+}  // namespace
 
 namespace {
 
@@ -781,7 +811,7 @@ void worker_loop(gsvd_ctx* h) {
     }
     gsvd_info info;
     std::memset(&info, 0, sizeof info);
-    solve_device(h->cfg, &r->prob, &info, ws, h_ctr, s);
+    solve_device(cfg_for(h, &r->prob), &r->prob, &info, ws, h_ctr, s);
     {
       std::lock_guard<std::mutex> lk(h->mu);
       r->info = info;
@@ -870,7 +900,7 @@ int gsvd_solve(gsvd_handle h, const gsvd_problem* p, gsvd_info* info) {
   }
   int pe = ensure_pinned(h);
   if (pe != GSVD_OK) return pe;
-  int st = solve_any(h->cfg, p, &tmp, h->ws, h->h_ctr, h->stream);
+  int st = solve_any(cfg_for(h, p), p, &tmp, h->ws, h->h_ctr, h->stream);
   if (info) *info = tmp;
   return st;
 }
@@ -914,7 +944,7 @@ int gsvd_solve_batched(gsvd_handle h, const gsvd_problem* ps, int32_t count, gsv
       unsigned long long* hc = nullptr;
       if (cudaMallocHost(&hc, NCTR * sizeof(unsigned long long)) == cudaSuccess) {
         for (int q = next.fetch_add(1); q < (int)blk.size(); q = next.fetch_add(1))
-          solve_device(h->cfg, &ps[blk[q]], &loc[blk[q]], ws, hc, s);
+          solve_device(cfg_for(h, &ps[blk[q]]), &ps[blk[q]], &loc[blk[q]], ws, hc, s);
         cudaFreeHost(hc);
       }
       cudaStreamSynchronize(s);
@@ -934,6 +964,71 @@ int gsvd_solve_batched(gsvd_handle h, const gsvd_problem* ps, int32_t count, gsv
   return first;
 }
 
+int gsvd_autotune(gsvd_handle h, int32_t dtype, int64_t m_f, int64_t m_g, int64_t n, int32_t* block_w) {
+  if (!h || !block_w || (dtype != GSVD_R64 && dtype != GSVD_C128) || n < 1 || m_f < n || m_g < n ||
+      n > 32768 || m_f > (int64_t)1 << 30 || m_g > (int64_t)1 << 30)
+    return GSVD_EINVAL;
+  *block_w = 0;
+  Plan P0;
+  if (!make_plan(h->cfg, dtype, m_f, m_g, n, P0)) return GSVD_EINVAL;
+  if (P0.path != GSVD_PATH_BLOCKED || h->cfg.block_w != 0) return GSVD_OK;  // nothing to choose
+  int pe = ensure_pinned(h);
+  if (pe != GSVD_OK) return pe;
+  const bool cplx = dtype == GSVD_C128;
+  const int E = cplx ? 2 : 1;
+  // a synthetic pair of this shape (hash-based values in [-1, 1))
+  DevBuf buf;
+  const size_t nF = (size_t)m_f * n * E, nG = (size_t)m_g * n * E, nZ = (size_t)n * n * E;
+  CK(buf.ensure(sizeof(double) * (nF + nG + nZ + 3 * (size_t)n) + 256));
+  double* F = static_cast<double*>(buf.p);
+  double* G = F + nF;
+  double* Z = G + nG;
+  double* v = Z + nZ;
+  gsvd_problem p;
+  std::memset(&p, 0, sizeof p);
+  p.dtype = dtype;
+  p.m_f = m_f; p.m_g = m_g; p.n = n;
+  p.F = F; p.ldf = m_f; p.G = G; p.ldg = m_g; p.Z = Z; p.ldz = n;
+  p.sigma_f = v; p.sigma_g = v + n; p.sigma = v + 2 * n;
+  const int cands_r[3] = {8, 16, 32}, cands_c[3] = {4, 8, 16};
+  double best_t = 1e300;
+  int best_w = 0;
+  for (int c = 0; c < 3; ++c) {
+    const int w = cplx ? cands_c[c] : cands_r[c];
+    if (2 * w > n || blk_vmax(w, cplx) == 0) continue;
+    gsvd_config cfg = h->cfg;
+    cfg.block_w = w;
+    cfg.path = GSVD_PATH_BLOCKED;
+    cfg.max_sweeps = 1;
+    cfg.fp32_max_sweeps = 1;
+    cfg.profile = 0;
+    double t = 0.0;
+    for (int rep = 0; rep < 2; ++rep) {  // the first run includes one-time set-up
+      CK(launch_fill_hash(E * m_f, n, 1u, F, E * m_f, h->stream));
+      CK(launch_fill_hash(E * m_g, n, 2u, G, E * m_g, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      gsvd_info info;
+      std::memset(&info, 0, sizeof info);
+      const auto t0 = std::chrono::steady_clock::now();
+      const int st = solve_device(cfg, &p, &info, h->ws, h->h_ctr, h->stream);
+      CK(cudaStreamSynchronize(h->stream));
+      t = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (st != GSVD_OK && st != GSVD_ENOCONV) return st;
+    }
+    if (t < best_t) {
+      best_t = t;
+      best_w = w;
+    }
+  }
+  if (best_w == 0) return GSVD_OK;
+  {
+    std::lock_guard<std::mutex> lk(h->tune_mu);
+    h->tuned[tune_key(h->cfg, dtype, m_f, m_g, n)] = best_w;
+  }
+  *block_w = best_w;
+  return GSVD_OK;
+}
+
 uint64_t gsvd_workspace_bytes(const gsvd_config* cfg, int32_t dtype, int64_t mf, int64_t mg, int64_t n) {
   gsvd_config c;
   if (cfg)
@@ -951,8 +1046,9 @@ int gsvd_submit(gsvd_handle h, const gsvd_problem* p, uint64_t* ticket) {
   if (v != GSVD_OK) return v;
   if (!(is_device_ptr(p->F) && is_device_ptr(p->G) && is_device_ptr(p->Z))) return GSVD_EINVAL;
   Plan P;
-  if (!make_plan(h->cfg, p->dtype, p->m_f, p->m_g, p->n, P)) return GSVD_EINVAL;
-  const uint64_t bytes = solve_bytes(h->cfg, P, p->m_f, p->m_g, p->n);
+  const gsvd_config pc = cfg_for(h, p);
+  if (!make_plan(pc, p->dtype, p->m_f, p->m_g, p->n, P)) return GSVD_EINVAL;
+  const uint64_t bytes = solve_bytes(pc, P, p->m_f, p->m_g, p->n);
   if (bytes > h->cfg.hbm_budget_bytes) return GSVD_ETOOBIG;
   std::unique_ptr<Request> r(new Request);
   r->prob = *p;

@@ -117,6 +117,8 @@ cudaError_t launch_identity(int n, bool cplx, bool fp32, void* Z, long long ldz,
 cudaError_t launch_gemm_f64_by_f32(int m, int n, bool cplx, const double* A, long long lda,
                                    const float* B, long long ldb, double* C, long long ldc,
                                    cudaStream_t s);
+// A (rows x n, column-major) <- deterministic pseudo-random values in [-1, 1)
+cudaError_t launch_fill_hash(int rows, int n, unsigned seed, double* A, long long lda, cudaStream_t s);
 // X(i, j) <- sf_i X(i, j) + sg_i T(i, j) (n x n): the right vectors from
 // U^T F (in X) and V^T G (in T)
 cudaError_t launch_rows_combine(int n, double* X, long long ldx, const double* sf, const double* T, long long ldt,

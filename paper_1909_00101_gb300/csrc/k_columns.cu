@@ -351,6 +351,27 @@ cudaError_t launch_rows_combine(int n, double* X, long long ldx, const double* s
   return cudaGetLastError();
 }
 
+// A (rows x n) <- deterministic values in [-1, 1): a 64-bit hash of the
+// element's index and the seed (SplitMix64's finaliser), the top 53 bits
+// taken as a fraction
+__global__ void k_fill_hash(int rows, int n, unsigned seed, double* A, long long lda) {
+  const int j = blockIdx.y;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
+    unsigned long long x = ((unsigned long long)seed << 48) ^ ((unsigned long long)j * rows + r);
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    x ^= x >> 31;
+    A[(size_t)j * lda + r] = (double)(x >> 11) * (1.0 / 4503599627370496.0) - 1.0;
+  }
+}
+
+cudaError_t launch_fill_hash(int rows, int n, unsigned seed, double* A, long long lda, cudaStream_t s) {
+  dim3 grid((rows + 255) / 256 < 64 ? (rows + 255) / 256 : 64, n);
+  k_fill_hash<<<grid, 256, 0, s>>>(rows, n, seed, A, lda);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rowscale(int n, bool cplx, const double* zdiag, const float* Z32, long long ld32, double* Z,
                             long long ldz, cudaStream_t s) {
   const int E = cplx ? 2 : 1;

@@ -80,6 +80,15 @@ def test_invalid_problems_rejected_before_any_launch(lib):
     assert lib.gsvd_solve(h, ctypes.byref(p), ctypes.byref(info)) == hz.EINVAL
     p.n = 4
     assert lib.gsvd_solve_batched(h, None, -1, None) == hz.EINVAL
+    # the autotuner checks its arguments before touching the GPU
+    w = ctypes.c_int32(-1)
+    assert lib.gsvd_autotune(h, 0, ctypes.c_int64(100), ctypes.c_int64(100), ctypes.c_int64(0), ctypes.byref(w)) == hz.EINVAL
+    assert lib.gsvd_autotune(h, 0, ctypes.c_int64(10), ctypes.c_int64(100), ctypes.c_int64(64), ctypes.byref(w)) == hz.EINVAL
+    assert lib.gsvd_autotune(h, 5, ctypes.c_int64(100), ctypes.c_int64(100), ctypes.c_int64(64), ctypes.byref(w)) == hz.EINVAL
+    assert lib.gsvd_autotune(h, 0, ctypes.c_int64(100), ctypes.c_int64(100), ctypes.c_int64(64), None) == hz.EINVAL
+    # a class that runs on the pointwise kernel has nothing to tune
+    assert lib.gsvd_autotune(h, 0, ctypes.c_int64(100), ctypes.c_int64(100), ctypes.c_int64(32), ctypes.byref(w)) == 0
+    assert w.value == 0
     # right vectors: real problems only, ld >= n
     X = np.zeros((4, 4), order="F")
     p.X, p.ldx = X.ctypes.data, 3

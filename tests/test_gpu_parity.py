@@ -256,6 +256,20 @@ def test_right_vectors_host_path(hz):
     assert np.array_equal(_np(d.X), h.X)
 
 
+# ------------------------------------------------------------ autotune ----
+
+def test_autotuned_width_is_used_by_later_solves(hz):
+    p = make_pair(600, 500, 256, seed=17)
+    with hz.Solver(path="auto") as s:
+        w = s.autotune(600, 500, 256)
+        assert w in (8, 16, 32)
+        r = s.solve(_dev(p.F), _dev(p.G))
+        assert r.info["block_w"] == w and r.info["path"] == 2
+    check(p.F, p.G, r, label="autotuned w=%d" % w)
+    with hz.Solver(path="auto") as s:
+        assert s.autotune(300, 260, 128, cplx=True) in (4, 8, 16)
+
+
 # ------------------------------------------------------ stripe driver ----
 
 def test_stripe_driver_with_the_library_pair_solver(hz):
