@@ -116,15 +116,28 @@ def prescale_stripes(F: np.ndarray, G: np.ndarray, p: int, q: int, w: int, n: in
     """Sec. 3.3 prescaling of two stripes (global stripes p and q of width w):
     z_j = 1 / ||g_j||, f_j *= z_j, g_j *= z_j, and Z0's columns for them
     (n x 2w, z_j in the global row of column j)."""
-    s = np.sqrt(np.sum(G * G, axis=0))
+    s = np.sqrt(np.sum(np.abs(G) ** 2, axis=0))
     if np.any(s == 0.0) or not np.all(np.isfinite(s)):
         raise ValueError("G is rank deficient")
     z = 1.0 / s
-    Z0 = np.zeros((n, 2 * w))
+    Z0 = np.zeros((n, 2 * w), dtype=np.result_type(F.dtype, G.dtype))
     cols = list(range(p * w, p * w + w)) + list(range(q * w, q * w + w))
     for j, c in enumerate(cols):
         Z0[c, j] = z[j]
     return F * z[None, :], G * z[None, :], Z0
+
+
+def _wire(x: np.ndarray):
+    import torch
+    x = np.ascontiguousarray(x)
+    if np.iscomplexobj(x):
+        return torch.from_numpy(np.ascontiguousarray(x.view(np.float64)))
+    return torch.from_numpy(x)
+
+
+def _unwire(t, cplx: bool) -> np.ndarray:
+    a = t.numpy()
+    return np.ascontiguousarray(a).view(np.complex128) if cplx else a
 
 
 def _run(F, G, Z, *, rank, world, dist, solve_pair, max_sweeps=30, timeout_s=30.0) -> StripeResult:
@@ -137,6 +150,7 @@ def _run(F, G, Z, *, rank, world, dist, solve_pair, max_sweeps=30, timeout_s=30.
     tmo = timedelta(seconds=timeout_s)
     # the pair's columns of F, G and Z stacked (rows x 2w), one buffer
     buf = np.concatenate([F, G, Z], axis=0)
+    cplx = np.iscomplexobj(buf)
     sweeps = 0
     for sweep in range(max_sweeps):
         big = 0
@@ -147,9 +161,9 @@ def _run(F, G, Z, *, rank, world, dist, solve_pair, max_sweeps=30, timeout_s=30.
             buf = buf @ Zpq
             big += int(b)
             # exchange: each local stripe to its holder in the next step
-            out = [torch.from_numpy(np.ascontiguousarray(buf[:, :w])),
-                   torch.from_numpy(np.ascontiguousarray(buf[:, w:]))]
-            inc = [torch.empty((rows, w), dtype=torch.float64) for _ in range(2)]
+            # (complex stripes travel as their real view)
+            out = [_wire(buf[:, :w]), _wire(buf[:, w:])]
+            inc = [torch.empty_like(out[0]) for _ in range(2)]
             src = senders(maps, k, rank)
             works = []
             local_copy = {}
@@ -170,7 +184,7 @@ def _run(F, G, Z, *, rank, world, dist, solve_pair, max_sweeps=30, timeout_s=30.
                     wk.wait(tmo)
             except RuntimeError:
                 return StripeResult(-6, sweeps, m.p, m.q, buf[:mf], buf[mf:mf + mg], buf[mf + mg:])
-            buf = np.concatenate([inc[0].numpy(), inc[1].numpy()], axis=1)
+            buf = np.concatenate([_unwire(inc[0], cplx), _unwire(inc[1], cplx)], axis=1)
         sweeps += 1
         tot = torch.tensor([big], dtype=torch.int64)
         try:
@@ -218,8 +232,8 @@ def finalize(F: np.ndarray, G: np.ndarray, Z: np.ndarray) -> dict:
     """Sec. 3.4 for a process's columns: Sigma_F = ||f_j||, Sigma_G = ||g_j||,
     Theta_j = (Sigma_F^2 + Sigma_G^2)^(-1/2), U = F / ||f||, V = G / ||g||,
     Z Theta, and Sigma = ||f_j|| / ||g_j|| (not sorted)."""
-    sf = np.sqrt(np.sum(F * F, axis=0))
-    sg = np.sqrt(np.sum(G * G, axis=0))
+    sf = np.sqrt(np.sum(np.abs(F) ** 2, axis=0))
+    sg = np.sqrt(np.sum(np.abs(G) ** 2, axis=0))
     th = 1.0 / np.sqrt(sf * sf + sg * sg)
     return {"U": F / sf[None, :], "V": G / sg[None, :], "Z": Z * th[None, :], "sigma_f": sf * th,
             "sigma_g": sg * th, "sigma": sf / sg}

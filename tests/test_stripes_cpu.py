@@ -85,17 +85,17 @@ def _spawn(world, F, G, w, out, fail_rank=-1):
     return [p.exitcode for p in ps]
 
 
-@pytest.mark.parametrize("world", [2, 3])
-def test_ranks_match_the_oracle(tmp_path, world):
+@pytest.mark.parametrize("world,cplx", [(2, False), (3, False), (2, True)])
+def test_ranks_match_the_oracle(tmp_path, world, cplx):
     import oracle
     from paper_1909_00101_gb300.inputs import make_pair
     w = 4
     n = 2 * world * w
-    p = make_pair(40, 36, n, lo=1e-2, hi=1e2, cond=10.0, seed=5)
+    p = make_pair(40, 36, n, lo=1e-2, hi=1e2, cond=10.0, cplx=cplx, seed=5)
     codes = _spawn(world, p.F, p.G, w, str(tmp_path))
     assert codes == [0] * world
     U = np.zeros_like(p.F)
-    Z = np.zeros((n, n))
+    Z = np.zeros((n, n), dtype=p.F.dtype)
     sf = np.zeros(n)
     sig = np.zeros(n)
     for r in range(world):
@@ -111,7 +111,7 @@ def test_ranks_match_the_oracle(tmp_path, world):
     ref = oracle.gsvd(p.F, p.G)
     got = np.sort(sig)[::-1]
     assert np.max(np.abs(got - ref["sigma"]) / ref["sigma"]) <= 1e-12
-    assert np.linalg.norm(U.T @ U - np.eye(n)) <= 1e-12 * n
+    assert np.linalg.norm(U.conj().T @ U - np.eye(n)) <= 1e-12 * n
     assert np.linalg.norm(p.F @ Z - U * sf[None, :]) / np.linalg.norm(p.F) <= 1e-13 * n
 
 
