@@ -6,6 +6,7 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -162,18 +163,20 @@ bool make_plan(const gsvd_config& cfg, int dtype, int64_t mf, int64_t mg, int64_
   // last wave costs little.  FP32 (latency-bound, short CTAs): about four per
   // SM, so that each CTA streams several tiles and the pivot kernel sums
   // fewer partials.
-  auto splits = [&](int per_sm, int& rf, int& rg) {
+  // The FP32 splits also serve the tensor-core FP64 Gram, whose split is
+  // one exact accumulation of at most OZ_K_MAX rows.
+  auto splits = [&](int per_sm, int max_tiles, int& rf, int& rg) {
     const int target = per_sm * 152;
     const int s = std::max(2, (target + P.nslots - 1) / P.nslots);
     const int tf = (int)((mf + 63) / 64), tg = (int)((mg + 63) / 64);
     const int sf = std::max(1, (int)std::lround((double)s * tf / (double)(tf + tg)));
     const int sg = std::max(1, s - sf);
-    const int pf = (tf + sf - 1) / sf, pg = (tg + sg - 1) / sg;  // tiles per split
-    rf = (tf + pf - 1) / pf;
+    const int pf = std::min(max_tiles, (tf + sf - 1) / sf), pg = std::min(max_tiles, (tg + sg - 1) / sg);
+    rf = (tf + pf - 1) / pf;  // tiles per split pf, pg
     rg = (tg + pg - 1) / pg;
   };
-  splits(12, P.rf, P.rg);
-  splits(4, P.rf32, P.rg32);
+  splits(12, INT_MAX, P.rf, P.rg);
+  splits(4, OZ_K_MAX / 64, P.rf32, P.rg32);
   const size_t V2 = (size_t)P.V * P.V;
   size_t o = 0;
   P.off_partial = o; o = align256(o + (size_t)P.nslots * std::max(P.rf + P.rg, P.rf32 + P.rg32) * V2 * 8);
@@ -480,11 +483,12 @@ size_t shortened_offset(const gsvd_config& cfg, int64_t n) {
   return (S.total + 255) & ~size_t(255);
 }
 // digit planes of the tensor-core products (fp64_gemm = 1): the largest of
-// the Grams F^T F (n x n over m rows) and the products m x n x n
+// the Grams F^T F (n x n over one piece of at most OZ_K_MAX of the m rows)
+// and the products m x n x n
 size_t shortened_oz_bytes(const gsvd_config& cfg, int64_t mf, int64_t mg, int64_t n) {
   if (cfg.fp64_gemm != 1) return 0;
   const int m = (int)std::max(mf, mg);
-  return std::max(dgemm_oz_ws_bytes((int)n, (int)n, m), dgemm_oz_ws_bytes(m, (int)n, (int)n));
+  return std::max(dgemm_oz_ws_bytes((int)n, (int)n, std::min(m, OZ_K_MAX)), dgemm_oz_ws_bytes(m, (int)n, (int)n));
 }
 size_t shortened_total(const gsvd_config& cfg, int64_t mf, int64_t mg, int64_t n) {
   return shortened_offset(cfg, n) + sizeof(double) * (4 * (size_t)n * n + (size_t)std::max(mf, mg) * n) + 256 +

@@ -133,6 +133,13 @@ struct OzWs {
   size_t bytes;
 };
 constexpr double OZ_GEMM_MIN = 1073741824.0;  // 2^30
+// Longest sum of slice products (rows of a Gram, K of a product) that one
+// accumulation may cover.  A level of seven digit products adds below
+// 7 * 2^16 per row; after K rows the FP32 high word holds below 7 * 2^16 K
+// and the low word, which collects a TwoSum error below 2^-24 of the high
+// word every 32 rows, below 7 K^2 / 2^13.  K <= 2^16 keeps the low word
+// under 2^22, so both words stay exact integers.
+constexpr int OZ_K_MAX = 65536;
 // FP64 GEMM: C = alpha op(A) op(B) + beta C (column-major); upper = 1:
 // only tiles meeting C's upper triangle are computed; upper = 2: also op(A)
 // and op(B) are upper triangular (square), so each tile sums its k range only
@@ -143,7 +150,8 @@ cudaError_t dgemm(bool ta, bool tb, int M, int N, int K, double alpha, const dou
 long long qr_launch_count();
 // the same product on the BF16 tensor cores with FP64 accuracy (operands
 // sliced once into digit planes in ws); cudaErrorInvalidValue if ws is
-// smaller than dgemm_oz_ws_bytes(M, N, K)
+// smaller than dgemm_oz_ws_bytes(M, N, K) or K > OZ_K_MAX (dgemm cuts a
+// longer K into pieces)
 size_t dgemm_oz_ws_bytes(int M, int N, int K);
 cudaError_t dgemm_oz(bool ta, bool tb, int M, int N, int K, double alpha, const double* A, long long lda,
                      const double* B, long long ldb, double beta, double* C, long long ldc, int upper, void* ws,

@@ -101,8 +101,8 @@ __device__ __forceinline__ long long float_int_to_ll(float f) {
 
 // sum_i x_i 2^(8(6 - i)) 2^e2 rounded to the nearest FP64 value (ties to
 // even), with integer operations only.  The sum is formed exactly as
-// H 2^32 + L (H signed 64-bit, L unsigned 32-bit); |x_i| < 2^40 and a normal
-// (or zero) result are assumed.
+// H 2^32 + L (H signed 64-bit, L unsigned 32-bit); |x_i| < 2^38 is assumed
+// (level sums over at most OZ_K_MAX rows are below 2^35).
 __device__ __forceinline__ double levels_to_double(const long long x[NLV], int e2) {
   const long long hi = (x[0] << 16) + (x[1] << 8) + x[2];
   const long long lo = (x[3] << 24) + (x[4] << 16) + (x[5] << 8) + x[6];
@@ -137,8 +137,13 @@ __device__ __forceinline__ double levels_to_double(const long long x[NLV], int e
     m >>= 1;
     ++ex;
   }
-  return __longlong_as_double((long long)((neg ? (1ull << 63) : 0ull) | ((unsigned long long)(ex + 1023) << 52) |
-                                          (m & 0xFFFFFFFFFFFFFull)));
+  // outside the normal range: below it the value is flushed to a signed
+  // zero (an entry below 2^-1022 is far under the product's error bound);
+  // above it, a signed infinity
+  const unsigned long long sign = neg ? (1ull << 63) : 0ull;
+  if (ex + 1023 <= 0) return __longlong_as_double((long long)sign);
+  if (ex + 1023 >= 2047) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(ex + 1023) << 52) | (m & 0xFFFFFFFFFFFFFull)));
 }
 
 __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2]) {
@@ -723,6 +728,9 @@ bool oz_supported(int V) { return V == 16 || V == 32; }
 
 cudaError_t launch_gram_oz(const BlkDims& d, const BlkBuffers& b, bool cplx, int step, cudaStream_t s) {
   const int V = blk_vmax(d.w, cplx);
+  // a row split is one exact accumulation: at most OZ_K_MAX rows
+  auto per = [](int m, int nsplit) { return ((m + 63) / 64 + nsplit - 1) / nsplit * 64; };
+  if (per(d.mf, d.rf) > OZ_K_MAX || per(d.mg, d.rg) > OZ_K_MAX) return cudaErrorInvalidValue;
   dim3 grid(d.nslots, d.rf + d.rg);
   if (V == 16) {
     if (cplx) k_gram_oz<16, true><<<grid, 32 * oz_gram_warps<16>(), 0, s>>>(d, b, step);
@@ -770,7 +778,7 @@ cudaError_t dgemm_oz(bool ta, bool tb, int M, int N, int K, double alpha, const 
                      const double* B, long long ldb, double beta, double* C, long long ldc, int upper, void* ws,
                      size_t ws_bytes, cudaStream_t s) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  if (!ws || ws_bytes < dgemm_oz_ws_bytes(M, N, K) || K <= 0) return cudaErrorInvalidValue;
+  if (!ws || K <= 0 || K > OZ_K_MAX || ws_bytes < dgemm_oz_ws_bytes(M, N, K)) return cudaErrorInvalidValue;
   const long long Kp = (long long)(K + 31) / 32 * 32;
   unsigned char* w = static_cast<unsigned char*>(ws);
   uint16_t* As = reinterpret_cast<uint16_t*>(w);

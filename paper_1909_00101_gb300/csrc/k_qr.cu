@@ -186,10 +186,21 @@ cudaError_t dgemm(bool ta, bool tb, int M, int N, int K, double alpha, const dou
   // row of op(A) times that of its column of op(B); every product here has
   // an op(A) with columns of one scale (Q, or F^T's rows as F's columns),
   // except the triangular R2 R1 (upper = 2), which stays on DMMA.
-  if (oz && oz->p && upper != 2 && (double)M * N * K >= OZ_GEMM_MIN && oz->bytes >= dgemm_oz_ws_bytes(M, N, K)) {
-    const bool same = ta && !tb && A == B && lda == ldb && M == N;
-    t_launches += same ? 2 : 3;
-    return dgemm_oz(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, upper, oz->p, oz->bytes, s);
+  if (oz && oz->p && upper != 2 && (double)M * N * K >= OZ_GEMM_MIN &&
+      oz->bytes >= dgemm_oz_ws_bytes(M, N, std::min(K, OZ_K_MAX))) {
+    // K in pieces of at most OZ_K_MAX (the longest exact level sum); each
+    // piece is rounded once and added to C
+    for (int k0 = 0; k0 < K; k0 += OZ_K_MAX) {
+      const int kc = std::min(OZ_K_MAX, K - k0);
+      const double* Ak = A + (ta ? (size_t)k0 : (size_t)k0 * lda);  // op(A)(:, k0 :)
+      const double* Bk = B + (tb ? (size_t)k0 * ldb : (size_t)k0);  // op(B)(k0 :, :)
+      const bool same = ta && !tb && Ak == Bk && lda == ldb && M == N;
+      t_launches += same ? 2 : 3;
+      const cudaError_t e = dgemm_oz(ta, tb, M, N, kc, alpha, Ak, lda, Bk, ldb, k0 ? 1.0 : beta, C, ldc, upper,
+                                     oz->p, oz->bytes, s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
   }
   dim3 grid((M + DM - 1) / DM, (N + DN - 1) / DN);
   ++t_launches;

@@ -131,6 +131,15 @@ def test_workspace_bytes_grows_with_size(lib):
     assert planes <= got_oz - got <= planes + 65536  # + the per-row scale exponents
     # complex problems are not shortened
     assert lib.gsvd_workspace_bytes(ctypes.byref(sh), 1, m, m, n) == c
+    # very tall pairs: the Grams are summed in pieces of at most 65536 rows,
+    # so the planes are those of the m x n x n products (7 digits x 2 bytes
+    # of the m x n operand and of the n x n one), not of the m-row Gram
+    # (+ one scale exponent per row of both operands)
+    n, m = 256, 200000
+    base = lib.gsvd_workspace_bytes(ctypes.byref(cfg), 0, n, n, n) + 8 * (4 * n * n + m * n)
+    extra = lib.gsvd_workspace_bytes(ctypes.byref(shoz), 0, m, m, n) - base
+    prod = 14 * m * n + 14 * n * n
+    assert prod <= extra <= prod + 4 * (m + n) + 2048 and extra < 2 * 7 * 2 * n * m
 
 
 def test_binding_structs_match_the_header(tmp_path):

@@ -451,3 +451,17 @@ def test_full_size_complex_3072x1024_mixed(hz):
     r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", precision="mixed", block_w=8, inner_max_sweeps=1,
                  max_sweeps=80, fp32_max_sweeps=80)
     _full_size_checks(hz, p, r)
+
+
+def test_shortened_products_longer_than_one_exact_sum(hz):
+    """m_F, m_G > 65536: the shortening's Grams F^T F and G^T G run on the
+    tensor cores in K pieces of at most 65536 rows (each summed exactly and
+    rounded once into C); the solve keeps the full-size tolerances against
+    the generated sigma and agrees with the unshortened solve."""
+    p = make_pair(70000, 66000, 128, seed=12)
+    a = hz.solve(_dev(p.F), _dev(p.G), path="blocked", block_w=16)
+    assert a.info["shortened"] == 1, a.info
+    _full_size_checks(hz, p, a)
+    b = hz.solve(_dev(p.F), _dev(p.G), path="blocked", block_w=16, shorten=0)
+    assert b.status == 0 and b.info["shortened"] == 0, b.info
+    assert rel_sigma_err(_np(a.sigma), _np(b.sigma)) <= 1e-12
