@@ -17,6 +17,9 @@ pair (p, q) the process holds and, for each of its two stripes, the target
 process encoded as -(t + 1) when the stripe becomes the target's first stripe
 and t + 1 when it becomes the second.
 
+n not divisible into 2 s stripes of one width is bordered first (border,
+unborder: Sec. 3.1, Sec. 4.1).
+
 This module is host logic only (no arithmetic of the method): the pair solver
 is passed in.  On GPUs it is the library's own solve of the pair; the tests
 run it on CPU ranks (gloo).  Any process that fails ends the others' waits by
@@ -125,6 +128,49 @@ def prescale_stripes(F: np.ndarray, G: np.ndarray, p: int, q: int, w: int, n: in
     for j, c in enumerate(cols):
         Z0[c, j] = z[j]
     return F * z[None, :], G * z[None, :], Z0
+
+
+def border(F: np.ndarray, G: np.ndarray, s: int, unit: int = 1) -> tuple:
+    """Bordering of Sec. 3.1 and Sec. 4.1: n is enlarged by k columns to a
+    multiple of 2 s unit, so that the 2 s stripes have one width, a multiple
+    of unit.  F and G each gain k rows and k columns; added column n + i has
+    a one in added row m_Y + i and zeros elsewhere.  The added columns keep
+    F and G of full column rank and are orthogonal to the original ones, so
+    no transformation mixes them in (their Gram couplings are exact zeros)
+    and each ends with the generalized singular value 1.  Returns (F, G, k);
+    k = 0 returns the inputs."""
+    if s < 1 or unit < 1:
+        raise ValueError("need s >= 1 and unit >= 1")
+    n = F.shape[1]
+    k = (-n) % (2 * s * unit)
+    if k == 0:
+        return F, G, 0
+
+    def grow(Y):
+        m = Y.shape[0]
+        B = np.zeros((m + k, n + k), dtype=Y.dtype, order="F")
+        B[:m, :n] = Y
+        B[m + np.arange(k), n + np.arange(k)] = 1.0
+        return B
+    return grow(F), grow(G), k
+
+
+def unborder(U: np.ndarray, V: np.ndarray, Z: np.ndarray, sigma_f: np.ndarray, sigma_g: np.ndarray,
+             sigma: np.ndarray, mf: int, mg: int, n: int) -> tuple:
+    """The GSVD of the original pair from that of the bordered one (columns in
+    any order, e.g. assembled from the processes' stripes): an added column
+    is one whose u_j lies in the added rows.  Original columns never mix
+    with added ones, so their U, V and Z have exact zeros in the added rows;
+    anything else raises ValueError.  Returns U (m_F x n), V (m_G x n),
+    Z (n x n) and the three sigma vectors, original columns in the given
+    order."""
+    added = np.any(U[mf:, :] != 0, axis=0)
+    keep = ~added
+    if int(keep.sum()) != n:
+        raise ValueError("expected %d original columns, found %d" % (n, int(keep.sum())))
+    if np.any(V[mg:, keep] != 0) or np.any(Z[n:, keep] != 0):
+        raise ValueError("an original column was mixed with an added one")
+    return U[:mf, keep], V[:mg, keep], Z[:n, keep], sigma_f[keep], sigma_g[keep], sigma[keep]
 
 
 def _wire(x: np.ndarray):

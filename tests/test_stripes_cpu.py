@@ -115,6 +115,65 @@ def test_ranks_match_the_oracle(tmp_path, world, cplx):
     assert np.linalg.norm(p.F @ Z - U * sf[None, :]) / np.linalg.norm(p.F) <= 1e-13 * n
 
 
+def _assemble(out, world, w, mf, mg, n, dtype):
+    U = np.zeros((mf, n), dtype=dtype)
+    V = np.zeros((mg, n), dtype=dtype)
+    Z = np.zeros((n, n), dtype=dtype)
+    sf, sg, sig = np.zeros(n), np.zeros(n), np.zeros(n)
+    for r in range(world):
+        d = np.load(os.path.join(out, "r%d.npz" % r))
+        assert int(d["status"]) == 0
+        for slot, stripe in ((0, int(d["p"])), (1, int(d["q"]))):
+            c = slice(stripe * w, stripe * w + w)
+            loc = slice(slot * w, slot * w + w)
+            U[:, c], V[:, c], Z[:, c] = d["U"][:, loc], d["V"][:, loc], d["Z"][:, loc]
+            sf[c], sg[c], sig[c] = d["sigma_f"][loc], d["sigma_g"][loc], d["sigma"][loc]
+    return U, V, Z, sf, sg, sig
+
+
+def test_bordering_shapes():
+    F = np.arange(12.0).reshape(4, 3)
+    G = np.arange(15.0).reshape(5, 3) + 1.0
+    Fb, Gb, k = S.border(F, G, 2, unit=2)           # n = 3 -> 8 (stripes of width 2)
+    assert k == 5 and Fb.shape == (9, 8) and Gb.shape == (10, 8)
+    assert np.array_equal(Fb[:4, :3], F) and np.array_equal(Gb[:5, :3], G)
+    assert np.array_equal(Fb[4:, 3:], np.eye(5)) and np.array_equal(Gb[5:, 3:], np.eye(5))
+    assert not Fb[:4, 3:].any() and not Fb[4:, :3].any() and not Gb[:5, 3:].any() and not Gb[5:, :3].any()
+    assert S.border(F, G, 3, unit=1)[2] == 3 and S.border(Fb, Gb, 2, unit=2)[2] == 0
+    with pytest.raises(ValueError):
+        S.border(F, G, 0)
+
+
+def test_bordered_ranks_match_the_oracle(tmp_path):
+    """n = 10 on two ranks, stripes of width 4: six added columns; after the
+    sweeps they are found and removed, and the original pair's GSVD remains."""
+    import oracle
+    from paper_1909_00101_gb300.inputs import make_pair
+    world, unit = 2, 4
+    p = make_pair(40, 36, 10, lo=1e-2, hi=1e2, cond=10.0, seed=15)
+    Fb, Gb, k = S.border(p.F, p.G, world, unit=unit)
+    nb = p.F.shape[1] + k
+    w = nb // (2 * world)
+    assert k == 6 and w == 4
+    codes = _spawn(world, Fb, Gb, w, str(tmp_path))
+    assert codes == [0] * world
+    full = _assemble(str(tmp_path), world, w, Fb.shape[0], Gb.shape[0], nb, Fb.dtype)
+    # every added column ends with sigma = 1 (unit f_j and g_j)
+    added = np.any(full[0][40:, :] != 0, axis=0)
+    assert int(added.sum()) == k and np.allclose(full[5][added], 1.0, rtol=0, atol=1e-15)
+    U, V, Z, sf, sg, sig = S.unborder(*full, 40, 36, 10)
+    ref = oracle.gsvd(p.F, p.G)
+    assert np.max(np.abs(np.sort(sig)[::-1] - ref["sigma"]) / ref["sigma"]) <= 1e-12
+    assert np.linalg.norm(U.T @ U - np.eye(10)) <= 1e-12 * 10
+    assert np.linalg.norm(p.F @ Z - U * sf[None, :]) / np.linalg.norm(p.F) <= 1e-13 * 10
+    assert np.linalg.norm(p.G @ Z - V * sg[None, :]) / np.linalg.norm(p.G) <= 1e-13 * 10
+    # a mixed column is refused
+    bad = [x.copy() for x in full]
+    bad[2][nb - 1, np.flatnonzero(~added)[0]] = 1e-300
+    with pytest.raises(ValueError):
+        S.unborder(*bad, 40, 36, 10)
+
+
 def test_a_failed_rank_ends_the_others_waits(tmp_path):
     from paper_1909_00101_gb300.inputs import make_pair
     world, w = 2, 4
