@@ -8,9 +8,12 @@
  *
  *   - pointwise (non-blocked), sequential row-cyclic pivot order
  *     (i = 0..n-2, j = i+1..n-1), the sequential strategy of Sec. 2.1;
- *   - variant 0 of Table "Variants" (Sec. 2.6): prescaling of F, G by
- *     Z0 = diag(1/||g_j||) (Sec. 2, "It is assumed that diag(B) = I"),
- *     pivot B-hat taken with unit diagonal, ordinary dot products;
+ *   - the variants of Table "Variants" (Sec. 2.6), one bit each:
+ *     variant 0: prescaling of F, G by Z0 = diag(1/||g_j||) (Sec. 2, the
+ *     diagonal of B assumed unit), pivot B-hat taken with unit diagonal,
+ *     ordinary dot products; +1: the enhanced dot products of App. A;
+ *     +2: no prescaling, each pivot pair rescaled by D-hat (Sec. 2.1) and
+ *     Z-hat = D-hat Z-hat'; +4: criterion C2;
  *   - per-step column sorting (Sec. 2.1, the P-hat permutation);
  *   - relative-orthogonality skip test (Sec. 2.1);
  *   - transformation Z-hat' by Sec. 2.1.1 (complex) or Sec. 2.1.2 (real),
@@ -46,6 +49,18 @@
  *       1/sqrt(||g_j||) printed in Sec. 2 does not make diag(B) = I.
  *   R8  Sigma_j = ||f_j|| / ||g_j||; the final sort is stable (ties keep
  *       the lower original column index first).
+ *   R9  D-hat variants: the sort after a transformation compares the
+ *       diagonal of Z-hat'^* A-hat' Z-hat' (= that of Z-hat^* A-hat Z-hat);
+ *       the printed formula pairs the D-scaled Z-hat with A-hat', which is
+ *       the same only when D-hat = I.  Without a transformation the sort
+ *       compares a'_ii = a_ii / b_ii and a'_jj.
+ *   R10 App. A: the product rounded toward -infinity is the largest value
+ *       not above a b; it is taken from the round-to-nearest product p and
+ *       its exact error a b - p (one fma), so no rounding-mode switch is
+ *       needed.  Complex data: the norms use the simpler of the two
+ *       enhanced procedures (the one the paper's variants use); the
+ *       off-diagonal complex dot products stay ordinary (App. A defines no
+ *       enhanced complex dot product).
  */
 #include <complex.h>
 #include <float.h>
@@ -78,6 +93,8 @@ typedef struct {
     int32_t criterion;  /* 1: C1, 2: C2 (Sec. 2.5)                          */
     int32_t max_pivots; /* > 0: stop after this many pivot pairs (a bounded
                            timing sample; the result is then HZO_ENOCONV)  */
+    int32_t enhanced;   /* 1: enhanced dot products (App. A; variant bit 1) */
+    int32_t dscale;     /* 1: D-hat rescaling, no prescaling (bit 2)        */
 } hzo_opts;
 
 typedef struct {
@@ -85,6 +102,8 @@ typedef struct {
     int32_t sweeps;     /* sweeps run, the last one without transformations */
     int64_t transf_all;
     int64_t transf_big;
+    int32_t presorted;  /* 1: the final sort found the columns in order      */
+    int32_t pad;
 } hzo_stats;
 
 /* sign(1, y) of the paper, reading R4 */
@@ -231,6 +250,140 @@ int HZO(hzo_pivot_cplx)(double a11, double a22, const double a12[2],
     return st;
 }
 
+/*
+ * D-hat of Sec. 2.1 (variants 2, 3, 6, 7), as the pivot step forms it: where
+ * b_kk != 1, a'_kk = a_kk / b_kk, D_kk = 1/sqrt(b_kk), and the off-diagonal
+ * a_ij, b_ij are multiplied by D_kk (first k = i, then k = j); elsewhere
+ * D_kk = 1.  Then A-hat' = D A-hat D, B-hat' = D B-hat D (up to rounding).
+ */
+static void dscale_r(real_t bii, real_t bjj, real_t *aii, real_t *ajj, real_t *aij, real_t *x,
+                     real_t *d1, real_t *d2)
+{
+    *d1 = 1;
+    *d2 = 1;
+    if (bii != 1) {
+        *aii = *aii / bii;
+        *d1 = 1 / sqrt(bii);
+        *aij *= *d1;
+        *x *= *d1;
+    }
+    if (bjj != 1) {
+        *ajj = *ajj / bjj;
+        *d2 = 1 / sqrt(bjj);
+        *aij *= *d2;
+        *x *= *d2;
+    }
+}
+
+static void dscale_c(real_t bii, real_t bjj, real_t *aii, real_t *ajj, cplx_t *aij, cplx_t *bij,
+                     real_t *d1, real_t *d2)
+{
+    *d1 = 1;
+    *d2 = 1;
+    if (bii != 1) {
+        *aii = *aii / bii;
+        *d1 = 1 / sqrt(bii);
+        *aij *= *d1;
+        *bij *= *d1;
+    }
+    if (bjj != 1) {
+        *ajj = *ajj / bjj;
+        *d2 = 1 / sqrt(bjj);
+        *aij *= *d2;
+        *bij *= *d2;
+    }
+}
+
+/* Z-hat = D-hat Z-hat': the first row of Z-hat' (row-major z[0], z[1]) times
+   D11, the second (z[2], z[3]) times D22 */
+static void drows_r(real_t z[4], real_t d1, real_t d2)
+{
+    z[0] *= d1;
+    z[1] *= d1;
+    z[2] *= d2;
+    z[3] *= d2;
+}
+
+static void drows_c(cplx_t z[4], real_t d1, real_t d2)
+{
+    z[0] *= d1;
+    z[1] *= d1;
+    z[2] *= d2;
+    z[3] *= d2;
+}
+
+/* exported D-hat pivots: Z-hat = D-hat Z-hat', for the invariant tests
+   Z^* B Z = I with b_ii, b_jj != 1 */
+int HZO(hzo_pivot_real_dscaled)(double a11, double a22, double a12, double b11, double b22,
+                                double b12, int32_t criterion, double zout[4], int32_t *small)
+{
+    real_t aii = a11, ajj = a22, aij = a12, x = b12, d1, d2, z[4];
+    int sm = 0;
+    dscale_r(b11, b22, &aii, &ajj, &aij, &x, &d1, &d2);
+    int st = pivot_real(aii, ajj, aij, x, criterion, z, &sm);
+    drows_r(z, d1, d2);
+    for (int k = 0; k < 4; ++k) zout[k] = (double)z[k];
+    *small = sm;
+    return st;
+}
+
+int HZO(hzo_pivot_cplx_dscaled)(double a11, double a22, const double a12[2], double b11,
+                                double b22, const double b12[2], int32_t criterion,
+                                double zout[8], int32_t *small)
+{
+    real_t aii = a11, ajj = a22, d1, d2;
+    cplx_t ca = (real_t)a12[0] + I * (real_t)a12[1];
+    cplx_t cb = (real_t)b12[0] + I * (real_t)b12[1];
+    cplx_t z[4];
+    int sm = 0;
+    dscale_c(b11, b22, &aii, &ajj, &ca, &cb, &d1, &d2);
+    int st = pivot_cplx(aii, ajj, ca, cb, criterion, z, &sm);
+    drows_c(z, d1, d2);
+    for (int k = 0; k < 4; ++k) {
+        zout[2 * k] = (double)creal(z[k]);
+        zout[2 * k + 1] = (double)cimag(z[k]);
+    }
+    *small = sm;
+    return st;
+}
+
+/* ------------------------------------------------- dot products (App. A) -- */
+
+/* the product a b rounded toward -infinity, reading R10 */
+static real_t mul_rd(real_t a, real_t b)
+{
+    real_t p = a * b;
+    real_t e = fma(a, b, -p);
+    return e < 0 ? nextafter(p, -INFINITY) : p;
+}
+
+/* enhanced real dot product: c_r = RD(a_r b_r), d_r = a_r b_r - c_r >= 0
+   (exact, by one fma); the sum of the c_r plus the sum of the d_r */
+static real_t dot_enh_rr(const real_t *a, const real_t *b, int64_t m)
+{
+    real_t sc = 0, sd = 0;
+    for (int64_t r = 0; r < m; ++r) {
+        real_t c = mul_rd(a[r], b[r]);
+        sc += c;
+        sd += fma(a[r], b[r], -c);
+    }
+    return sc + sd;
+}
+
+/* enhanced ||a||^2 of a complex vector, the simpler procedure of App. A:
+   per element e = d_re + d_im, then (e + the smaller c) + the larger c */
+static real_t nrm2sq_enh_c(const cplx_t *a, int64_t m)
+{
+    real_t s = 0;
+    for (int64_t r = 0; r < m; ++r) {
+        real_t re = creal(a[r]), im = cimag(a[r]);
+        real_t cr = mul_rd(re, re), ci = mul_rd(im, im);
+        real_t e = fma(re, re, -cr) + fma(im, im, -ci);
+        s += (cr <= ci) ? (e + cr) + ci : (e + ci) + cr;
+    }
+    return s;
+}
+
 /* ---------------------------------------------------------------- real -- */
 
 static real_t dot_rr(const real_t *a, const real_t *b, int64_t m)
@@ -238,6 +391,12 @@ static real_t dot_rr(const real_t *a, const real_t *b, int64_t m)
     real_t s = 0;
     for (int64_t r = 0; r < m; ++r) s += a[r] * b[r];
     return s;
+}
+
+/* a^T b, ordinary or enhanced (variants 1, 3, 5, 7) */
+static real_t dot_r(const hzo_opts *opt, const real_t *a, const real_t *b, int64_t m)
+{
+    return opt->enhanced ? dot_enh_rr(a, b, m) : dot_rr(a, b, m);
 }
 
 static void swap_cols_r(real_t *Y, int64_t m, int64_t i, int64_t j)
@@ -291,10 +450,15 @@ int HZO(hzo_gsvd_real)(int64_t mf, int64_t mg, int64_t n,
         if (!isfinite(g[k])) status = HZO_EINVAL;
     if (status != HZO_OK) goto done;
 
-    /* prescaling: Z0 = diag(1/||g_j||), F0 = F Z0, G0 = G Z0 (reading R7) */
+    /* prescaling: Z0 = diag(1/||g_j||), F0 = F Z0, G0 = G Z0 (reading R7);
+       the D-hat variants start from Z0 = I */
     for (int64_t j = 0; j < n; ++j) {
-        real_t s = dot_rr(&g[j * mg], &g[j * mg], mg);
+        real_t s = dot_r(opt, &g[j * mg], &g[j * mg], mg);
         if (!(s > 0)) { status = HZO_ENOTPD; goto done; }
+        if (opt->dscale) {
+            z[j * n + j] = 1;
+            continue;
+        }
         real_t zj = 1 / sqrt(s);
         for (int64_t r = 0; r < mf; ++r) f[j * mf + r] *= zj;
         for (int64_t r = 0; r < mg; ++r) g[j * mg + r] *= zj;
@@ -319,10 +483,16 @@ int HZO(hzo_gsvd_real)(int64_t mf, int64_t mg, int64_t n,
                 }
                 real_t *fi = &f[i * mf], *fj = &f[j * mf];
                 real_t *gi = &g[i * mg], *gj = &g[j * mg];
-                real_t aii = dot_rr(fi, fi, mf);
-                real_t ajj = dot_rr(fj, fj, mf);
-                real_t aij = dot_rr(fi, fj, mf);
-                real_t x = dot_rr(gi, gj, mg);
+                real_t aii = dot_r(opt, fi, fi, mf);
+                real_t ajj = dot_r(opt, fj, fj, mf);
+                real_t aij = dot_r(opt, fi, fj, mf);
+                real_t x = dot_r(opt, gi, gj, mg);
+                real_t d1 = 1, d2 = 1;
+                if (opt->dscale) {
+                    real_t bii = dot_r(opt, gi, gi, mg), bjj = dot_r(opt, gj, gj, mg);
+                    if (!(bii > 0) || !(bjj > 0)) { status = HZO_ENOTPD; goto done; }
+                    dscale_r(bii, bjj, &aii, &ajj, &aij, &x, &d1, &d2);
+                }
                 /* relative orthogonality (Sec. 2.1) */
                 if (fabs(aij) < sqrt(aii) * sqrt(ajj) * tol && fabs(x) < tol) {
                     if (opt->sort && aii < ajj) {
@@ -338,13 +508,14 @@ int HZO(hzo_gsvd_real)(int64_t mf, int64_t mg, int64_t n,
                 if (status != HZO_OK) goto done;
                 ++nall;
                 nbig += !small;
+                /* transformed diagonal of A-hat (Sec. 3.5.3, real case), reading R9 */
+                real_t a1 = zh[0] * zh[0] * aii + 2 * zh[0] * zh[2] * aij + zh[2] * zh[2] * ajj;
+                real_t a2 = zh[1] * zh[1] * aii + 2 * zh[3] * zh[1] * aij + zh[3] * zh[3] * ajj;
+                drows_r(zh, d1, d2); /* Z-hat = D-hat Z-hat' */
                 rot_cols_r(f, mf, i, j, zh);
                 rot_cols_r(g, mg, i, j, zh);
                 rot_cols_r(z, n, i, j, zh);
                 if (opt->sort) {
-                    /* transformed diagonal of A-hat (Sec. 3.5.3, real case) */
-                    real_t a1 = zh[0] * zh[0] * aii + 2 * zh[0] * zh[2] * aij + zh[2] * zh[2] * ajj;
-                    real_t a2 = zh[1] * zh[1] * aii + 2 * zh[3] * zh[1] * aij + zh[3] * zh[3] * ajj;
                     if (a1 < a2) {
                         swap_cols_r(f, mf, i, j);
                         swap_cols_r(g, mg, i, j);
@@ -362,8 +533,8 @@ int HZO(hzo_gsvd_real)(int64_t mf, int64_t mg, int64_t n,
 
     /* final rescaling (Sec. 2.4) */
     for (int64_t j = 0; j < n; ++j) {
-        nf[j] = sqrt(dot_rr(&f[j * mf], &f[j * mf], mf));
-        ng[j] = sqrt(dot_rr(&g[j * mg], &g[j * mg], mg));
+        nf[j] = sqrt(dot_r(opt, &f[j * mf], &f[j * mf], mf));
+        ng[j] = sqrt(dot_r(opt, &g[j * mg], &g[j * mg], mg));
         perm[j] = j;
     }
     /* stable insertion sort of indices by descending Sigma (reading R8) */
@@ -377,6 +548,8 @@ int HZO(hzo_gsvd_real)(int64_t mf, int64_t mg, int64_t n,
         }
         perm[b + 1] = p;
     }
+    st->presorted = 1;
+    for (int64_t k = 0; k < n; ++k) if (perm[k] != k) st->presorted = 0;
     for (int64_t k = 0; k < n; ++k) {
         int64_t j = perm[k];
         real_t th = 1 / sqrt(nf[j] * nf[j] + ng[j] * ng[j]);
@@ -409,6 +582,12 @@ static real_t nrm2sq_c(const cplx_t *a, int64_t m)
     real_t s = 0;
     for (int64_t r = 0; r < m; ++r) s += creal(a[r]) * creal(a[r]) + cimag(a[r]) * cimag(a[r]);
     return s;
+}
+
+/* ||a||^2, ordinary or enhanced (variants 1, 3, 5, 7) */
+static real_t nrm2sq_cv(const hzo_opts *opt, const cplx_t *a, int64_t m)
+{
+    return opt->enhanced ? nrm2sq_enh_c(a, m) : nrm2sq_c(a, m);
 }
 
 static void swap_cols_c(cplx_t *Y, int64_t m, int64_t i, int64_t j)
@@ -460,8 +639,12 @@ int HZO(hzo_gsvd_cplx)(int64_t mf, int64_t mg, int64_t n,
     if (status != HZO_OK) goto done;
 
     for (int64_t j = 0; j < n; ++j) {
-        real_t s = nrm2sq_c(&g[j * mg], mg);
+        real_t s = nrm2sq_cv(opt, &g[j * mg], mg);
         if (!(s > 0)) { status = HZO_ENOTPD; goto done; }
+        if (opt->dscale) {
+            z[j * n + j] = 1;
+            continue;
+        }
         real_t zj = 1 / sqrt(s);
         for (int64_t r = 0; r < mf; ++r) f[j * mf + r] *= zj;
         for (int64_t r = 0; r < mg; ++r) g[j * mg + r] *= zj;
@@ -486,10 +669,16 @@ int HZO(hzo_gsvd_cplx)(int64_t mf, int64_t mg, int64_t n,
                 }
                 cplx_t *fi = &f[i * mf], *fj = &f[j * mf];
                 cplx_t *gi = &g[i * mg], *gj = &g[j * mg];
-                real_t aii = nrm2sq_c(fi, mf);
-                real_t ajj = nrm2sq_c(fj, mf);
+                real_t aii = nrm2sq_cv(opt, fi, mf);
+                real_t ajj = nrm2sq_cv(opt, fj, mf);
                 cplx_t aij = dot_cc(fi, fj, mf);
                 cplx_t bij = dot_cc(gi, gj, mg);
+                real_t d1 = 1, d2 = 1;
+                if (opt->dscale) {
+                    real_t bii = nrm2sq_cv(opt, gi, mg), bjj = nrm2sq_cv(opt, gj, mg);
+                    if (!(bii > 0) || !(bjj > 0)) { status = HZO_ENOTPD; goto done; }
+                    dscale_c(bii, bjj, &aii, &ajj, &aij, &bij, &d1, &d2);
+                }
                 real_t abs_a = hypot(creal(aij), cimag(aij));
                 real_t abs_b = hypot(creal(bij), cimag(bij));
                 if (abs_a < sqrt(aii) * sqrt(ajj) * tol && abs_b < tol) {
@@ -506,12 +695,13 @@ int HZO(hzo_gsvd_cplx)(int64_t mf, int64_t mg, int64_t n,
                 if (status != HZO_OK) goto done;
                 ++nall;
                 nbig += !small;
+                drows_c(zh, d1, d2); /* Z-hat = D-hat Z-hat' */
                 rot_cols_c(f, mf, i, j, zh);
                 rot_cols_c(g, mg, i, j, zh);
                 rot_cols_c(z, n, i, j, zh);
                 if (opt->sort) {
                     /* complex case: recompute the transformed norms (Sec. 3.5.3) */
-                    if (nrm2sq_c(fi, mf) < nrm2sq_c(fj, mf)) {
+                    if (nrm2sq_cv(opt, fi, mf) < nrm2sq_cv(opt, fj, mf)) {
                         swap_cols_c(f, mf, i, j);
                         swap_cols_c(g, mg, i, j);
                         swap_cols_c(z, n, i, j);
@@ -527,8 +717,8 @@ int HZO(hzo_gsvd_cplx)(int64_t mf, int64_t mg, int64_t n,
     if (!converged) status = HZO_ENOCONV;
 
     for (int64_t j = 0; j < n; ++j) {
-        nf[j] = sqrt(nrm2sq_c(&f[j * mf], mf));
-        ng[j] = sqrt(nrm2sq_c(&g[j * mg], mg));
+        nf[j] = sqrt(nrm2sq_cv(opt, &f[j * mf], mf));
+        ng[j] = sqrt(nrm2sq_cv(opt, &g[j * mg], mg));
         perm[j] = j;
     }
     for (int64_t a = 1; a < n; ++a) {
@@ -541,6 +731,8 @@ int HZO(hzo_gsvd_cplx)(int64_t mf, int64_t mg, int64_t n,
         }
         perm[b + 1] = p;
     }
+    st->presorted = 1;
+    for (int64_t k = 0; k < n; ++k) if (perm[k] != k) st->presorted = 0;
     for (int64_t k = 0; k < n; ++k) {
         int64_t j = perm[k];
         real_t th = 1 / sqrt(nf[j] * nf[j] + ng[j] * ng[j]);
@@ -567,4 +759,27 @@ done:
     st->status = status;
     free(f); free(g); free(z); free(nf); free(ng); free(perm);
     return status;
+}
+
+/* exported dot products (for the closed-form pins of App. A) */
+double HZO(hzo_dot_real)(const double *a, const double *b, int64_t m, int32_t enhanced)
+{
+    real_t *x = malloc(sizeof(real_t) * (m > 0 ? m : 1)), *y = malloc(sizeof(real_t) * (m > 0 ? m : 1));
+    for (int64_t r = 0; r < m; ++r) {
+        x[r] = a[r];
+        y[r] = b[r];
+    }
+    real_t s = enhanced ? dot_enh_rr(x, y, m) : dot_rr(x, y, m);
+    free(x);
+    free(y);
+    return (double)s;
+}
+
+double HZO(hzo_nrm2sq_cplx)(const double *a, int64_t m, int32_t enhanced)
+{
+    cplx_t *x = malloc(sizeof(cplx_t) * (m > 0 ? m : 1));
+    for (int64_t r = 0; r < m; ++r) x[r] = (real_t)a[2 * r] + I * (real_t)a[2 * r + 1];
+    real_t s = enhanced ? nrm2sq_enh_c(x, m) : nrm2sq_c(x, m);
+    free(x);
+    return (double)s;
 }

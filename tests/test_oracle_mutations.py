@@ -1,9 +1,10 @@
 """The oracle pins have teeth: a plausible mistake planted in a copy of the
 oracle (on the CPU only) makes at least one pin fail.
 
-Each mutation is a one-token edit of hz_oracle.c (a flipped sign, a dropped
-term, a swapped index or operand); the mutated copy is compiled into a
-temporary library and run through a quick subset of the pins.
+Each mutation is a small edit of hz_oracle.c (a flipped sign, a dropped
+term, a swapped index or operand, two statements in the wrong order); the
+mutated copy is compiled into a temporary library and run through a quick
+subset of the pins.
 """
 import json
 import os
@@ -35,6 +36,19 @@ MUTATIONS = [
     ("cplx_conj_missing", "for (int64_t r = 0; r < m; ++r) s += conj(a[r]) * b[r];", "for (int64_t r = 0; r < m; ++r) s += a[r] * b[r];"),
     ("cplx_psi_sign", "real_t cpsi = r2 * sqrt(1 - x * s2 + t * cg * c2);", "real_t cpsi = r2 * sqrt(1 + x * s2 + t * cg * c2);"),
     ("cplx_tau", "real_t tau = sgn1(h);", "real_t tau = 1;"),
+    # variants (Table "Variants"): App. A dot products and the D-hat rescaling
+    ("enh_d_sign", "sd += fma(a[r], b[r], -c);", "sd -= fma(a[r], b[r], -c);"),
+    ("enh_cplx_e_dropped", "real_t e = fma(re, re, -cr) + fma(im, im, -ci);", "real_t e = 0 * fma(re, re, -cr);"),
+    ("dscale_mul", "*aii = *aii / bii;", "*aii = *aii * bii;"),
+    ("dscale_x_index", "*aij *= *d1;\n        *x *= *d1;", "*aij *= *d1;\n        *x *= *d2;"),
+    ("drows_swapped", "z[2] *= d2;\n    z[3] *= d2;\n}\n\nstatic void drows_c", "z[2] *= d1;\n    z[3] *= d2;\n}\n\nstatic void drows_c"),
+    ("sort_with_dscaled_z",
+     "real_t a1 = zh[0] * zh[0] * aii + 2 * zh[0] * zh[2] * aij + zh[2] * zh[2] * ajj;\n"
+     "                real_t a2 = zh[1] * zh[1] * aii + 2 * zh[3] * zh[1] * aij + zh[3] * zh[3] * ajj;\n"
+     "                drows_r(zh, d1, d2);",
+     "drows_r(zh, d1, d2);\n"
+     "                real_t a1 = zh[0] * zh[0] * aii + 2 * zh[0] * zh[2] * aij + zh[2] * zh[2] * ajj;\n"
+     "                real_t a2 = zh[1] * zh[1] * aii + 2 * zh[3] * zh[1] * aij + zh[3] * zh[3] * ajj;"),
 ]
 
 
@@ -70,12 +84,46 @@ def _pins_pass(lib) -> bool:
         return False
     for cplx in (False, True):
         p = make_pair(24, 20, 12, cplx=cplx, seed=5)
-        r = oracle.gsvd(p.F, p.G, lib=lib)
-        if r["status"] != 0 or rel_sigma_err(r["sigma"], p.sigma) > 1e-10:
+        for variant in (0, 3):
+            r = oracle.gsvd(p.F, p.G, variant=variant, lib=lib)
+            if r["status"] != 0 or rel_sigma_err(r["sigma"], p.sigma) > 1e-10 or not r["presorted"]:
+                return False
+            inv = invariants(p.F, p.G, r["U"], r["V"], r["Z"], r["sigma_f"], r["sigma_g"], r["sigma"])
+            if not (inv["FZ"] < 1e-12 and inv["GZ"] < 1e-12 and inv["UU"] < 1e-12 and inv["VV"] < 1e-12
+                    and inv["scale"] <= 8 * eps and inv["sorted"]):
+                return False
+    return _variant_pins_pass(lib)
+
+
+def _variant_pins_pass(lib) -> bool:
+    """Quick subset of the variant pins: App. A closed form and bound, the
+    sort after one D-hat transformation, D-hat pivot invariants."""
+    from fractions import Fraction
+    x = 1.0 + 2.0 ** -27
+    if oracle.dot_real([x, 1.0], [x, -(1.0 + 2.0 ** -26)], enhanced=True, lib=lib) != 2.0 ** -54:
+        return False
+    rng = np.random.default_rng(12)
+    u = Fraction(2.0 ** -53)
+    for _ in range(3000):
+        re, im = rng.standard_normal(2)
+        ex = Fraction(float(re)) ** 2 + Fraction(float(im)) ** 2
+        got = Fraction(oracle.nrm2sq_cplx([complex(re, im)], enhanced=True, lib=lib))
+        if abs(got - ex) > (Fraction(3, 2) * u + 4 * u * u) * ex:
             return False
-        inv = invariants(p.F, p.G, r["U"], r["V"], r["Z"], r["sigma_f"], r["sigma_g"], r["sigma"])
-        if not (inv["FZ"] < 1e-12 and inv["GZ"] < 1e-12 and inv["UU"] < 1e-12 and inv["VV"] < 1e-12
-                and inv["scale"] <= 8 * eps and inv["sorted"]):
+    for t in range(60):
+        p = make_pair(5, 4, 2, lo=1.0, hi=1.2, cond=3.0, seed=100 + t)
+        d = np.exp(rng.uniform(-4, 4, 2))
+        if not oracle.gsvd(p.F * d[None, :], p.G * d[None, :], variant=2, max_sweeps=1, lib=lib)["presorted"]:
+            return False
+    eps = 2.0 ** -53
+    for _ in range(100):
+        f = rng.standard_normal((6, 2)) * np.exp(rng.uniform(-3, 3, 2))[None, :]
+        g = rng.standard_normal((6, 2)) * np.exp(rng.uniform(-3, 3, 2))[None, :]
+        A, B = f.T @ f, g.T @ g
+        Z, _, st = oracle.pivot_real_dscaled(A[0, 0], A[1, 1], A[0, 1], B[0, 0], B[1, 1], B[0, 1], lib=lib)
+        bound = 64 * eps * np.linalg.norm(Z) ** 2
+        if st != 0 or abs((Z.T @ A @ Z)[0, 1]) > bound * np.linalg.norm(A) or \
+                np.max(np.abs(Z.T @ B @ Z - np.eye(2))) > bound * np.linalg.norm(B):
             return False
     return True
 

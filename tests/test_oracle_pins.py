@@ -297,3 +297,143 @@ def test_nearly_parallel_G_gives_huge_sigma():
     G[:, 1] = 2.0 * G[:, 0]
     r = oracle.gsvd(F, G)
     assert r["status"] == -4 or r["sigma"][0] > 1e12
+
+
+# ------------------------------------------- variants (Table "Variants") --
+
+def test_enhanced_real_dot_closed_forms():
+    """App. A: c = RD(a b) and d = a b - c >= 0 split every product exactly,
+    so a sum that cancels to a product's rounding error comes out exact,
+    where the ordinary dot product returns the rounded products' sum."""
+    from fractions import Fraction
+    x = 1.0 + 2.0 ** -27                      # x^2 = 1 + 2^-26 + 2^-54: rounding error +2^-54
+    a, b = [x, 1.0], [x, -(1.0 + 2.0 ** -26)]
+    assert oracle.dot_real(a, b) == 0.0
+    assert oracle.dot_real(a, b, enhanced=True) == 2.0 ** -54
+    rng = np.random.default_rng(21)
+    hits = 0
+    for _ in range(200):                      # either sign of the product's rounding error
+        y = float(rng.uniform(1.0, 2.0))
+        p = y * y
+        exact = Fraction(y) * Fraction(y) - Fraction(p)
+        got = oracle.dot_real([y, 1.0], [y, -p], enhanced=True)
+        assert Fraction(got) == exact
+        hits += exact < 0
+    assert 20 < hits < 180
+    # exact products (small integers): both forms give the exact sum
+    ia = rng.integers(-1000, 1000, 64).astype(float)
+    ib = rng.integers(-1000, 1000, 64).astype(float)
+    assert oracle.dot_real(ia, ib) == oracle.dot_real(ia, ib, enhanced=True) == float(np.dot(ia, ib))
+    # random vectors: within the dot product's bound of the exact value
+    for m in (1, 7, 100):
+        va, vb = rng.standard_normal(m), rng.standard_normal(m)
+        exact = sum(Fraction(float(p)) * Fraction(float(q)) for p, q in zip(va, vb))
+        scale = sum(abs(Fraction(float(p)) * Fraction(float(q))) for p, q in zip(va, vb))
+        got = Fraction(oracle.dot_real(va, vb, enhanced=True))
+        assert abs(got - exact) <= (m + 2) * Fraction(EPS) * scale
+
+
+def test_enhanced_complex_norm_bound():
+    """App. A, the simpler procedure for ||a||^2: per element
+    s = (e + c_small) + c_large with e = d_re + d_im is within 1.5 u (+ O(u^2))
+    of |a|^2 (one rounding of e + c_small, at most half the total, and one of
+    the sum); the ordinary re^2 + im^2 needs the 2 u bound."""
+    from fractions import Fraction
+    rng = np.random.default_rng(22)
+    u = Fraction(EPS)
+    worst_ord = Fraction(0)
+    for _ in range(20000):
+        re, im = rng.standard_normal(2) * math.exp(rng.uniform(-5, 5))
+        ex = Fraction(float(re)) ** 2 + Fraction(float(im)) ** 2
+        got = Fraction(oracle.nrm2sq_cplx([complex(re, im)], enhanced=True))
+        assert abs(got - ex) <= (Fraction(3, 2) * u + 4 * u * u) * ex, (re, im)
+        worst_ord = max(worst_ord, abs(Fraction(oracle.nrm2sq_cplx([complex(re, im)])) - ex) / ex)
+    assert worst_ord > Fraction(3, 2) * u     # the ordinary form does exceed it
+    v = rng.standard_normal(50) + 1j * rng.standard_normal(50)
+    ex = sum(Fraction(float(z.real)) ** 2 + Fraction(float(z.imag)) ** 2 for z in v)
+    got = Fraction(oracle.nrm2sq_cplx(v, enhanced=True))
+    assert abs(got - ex) <= 52 * u * ex
+
+
+def _dscaled_grid(rng, cplx):
+    f = rng.standard_normal((6, 2)) * np.exp(rng.uniform(-3, 3, 2))[None, :]
+    g = rng.standard_normal((6, 2)) * np.exp(rng.uniform(-3, 3, 2))[None, :]
+    if cplx:
+        f = f + 1j * rng.standard_normal((6, 2))
+        g = g + 1j * rng.standard_normal((6, 2))
+    return f.conj().T @ f, g.conj().T @ g
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_dscaled_pivot_invariants(cplx):
+    """D-hat variants (Sec. 2.1): with b_ii, b_jj != 1, Z-hat = D Z-hat' still
+    makes Z^* B Z = I and Z^* A Z diagonal for the unscaled pivot A, B."""
+    rng = np.random.default_rng(23 + cplx)
+    for _ in range(500):
+        A, B = _dscaled_grid(rng, cplx)
+        if cplx:
+            Z, _, st = oracle.pivot_cplx_dscaled(A[0, 0].real, A[1, 1].real, A[0, 1], B[0, 0].real, B[1, 1].real,
+                                                 B[0, 1])
+        else:
+            Z, _, st = oracle.pivot_real_dscaled(A[0, 0], A[1, 1], A[0, 1], B[0, 0], B[1, 1], B[0, 1])
+        assert st == 0
+        ZA = Z.conj().T @ A @ Z
+        ZB = Z.conj().T @ B @ Z
+        assert abs(ZA[0, 1]) <= _bound(Z, A) and np.max(np.abs(ZB - np.eye(2))) <= _bound(Z, B)
+
+
+def test_dscaled_pivot_reduces_to_unscaled_at_unit_diagonal():
+    """b_ii = b_jj = 1 exactly: D-hat = I, and the transformation is the unscaled one bit for bit."""
+    rng = np.random.default_rng(25)
+    for _ in range(100):
+        a11, a22 = rng.uniform(0.1, 10, 2)
+        a12, x = rng.uniform(-1, 1) * math.sqrt(a11 * a22), rng.uniform(-0.9, 0.9)
+        Z0, s0, _ = oracle.pivot_real(a11, a22, a12, x)
+        Z1, s1, _ = oracle.pivot_real_dscaled(a11, a22, a12, 1.0, 1.0, x)
+        assert np.array_equal(Z0, Z1) and s0 == s1
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("variant", range(1, 8))
+def test_variants_known_sigma_and_invariants(cplx, variant):
+    """Every variant of Table "Variants" reaches the generated sigma and the
+    invariants; with the per-step sort the columns end in descending order
+    (the final sort finds them presorted), which in the D-hat variants needs
+    the sort to compare a_ii / b_ii, not a_ii."""
+    for seed, (mf, mg, n) in enumerate([(40, 30, 24), (30, 50, 17)]):
+        p = make_pair(mf, mg, n, lo=1e-2, hi=1e2, cond=1e2, cplx=cplx, seed=seed)
+        r = oracle.gsvd(p.F, p.G, variant=variant)
+        assert r["status"] == 0
+        assert rel_sigma_err(r["sigma"], p.sigma) < 1e4 * n * EPS * 1e2
+        inv = invariants(p.F, p.G, r["U"], r["V"], r["Z"], r["sigma_f"], r["sigma_g"], r["sigma"])
+        assert inv["FZ"] < 1e-13 * n and inv["GZ"] < 1e-13 * n
+        assert inv["UU"] < 1e-12 and inv["VV"] < 1e-12
+        assert inv["scale"] <= 8 * EPS and inv["sorted"]
+        assert r["presorted"], (variant, seed)
+        ref = oracle.gsvd(p.F, p.G, extended=True)
+        assert rel_sigma_err(r["sigma"], ref["sigma"]) < 1e-12
+
+
+@pytest.mark.parametrize("variant", range(8))
+def test_one_transformation_sorts_the_pair(variant):
+    """n = 2, one sweep: the single transformation diagonalises the pair and
+    the sort after it (Sec. 2.1) puts the larger sigma first.  Columns of F
+    and G scaled alike (sigma unchanged, b_jj far from 1) and sigma within a
+    factor 1.2 make a sort on the wrong diagonal show."""
+    rng = np.random.default_rng(33)
+    for t in range(100):
+        p = make_pair(5, 4, 2, lo=1.0, hi=1.2, cond=3.0, seed=100 + t)
+        d = np.exp(rng.uniform(-4, 4, 2))
+        r = oracle.gsvd(p.F * d[None, :], p.G * d[None, :], variant=variant, max_sweeps=1)
+        assert r["sweeps"] == 1 and r["presorted"], (variant, t)
+
+
+@pytest.mark.parametrize("variant", range(8))
+def test_variants_appendix_g(variant):
+    """Appendix G's pair (cond(G) = 4e10) in every variant: sigma within 4 eps."""
+    gold = json.load(open(os.path.join(GOLD, "appG_4x4.json")))
+    F = np.array(gold["F"], dtype=float)
+    G = np.array(gold["G"], dtype=float)
+    exact = np.sqrt(np.array(gold["lambda_exact_sorted_ascending"]))[::-1]
+    r = oracle.gsvd(F, G, variant=variant)
+    assert r["status"] == 0 and rel_sigma_err(r["sigma"], exact) <= 4 * EPS
