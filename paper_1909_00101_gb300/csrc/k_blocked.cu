@@ -803,14 +803,14 @@ __global__ void __launch_bounds__(INNER_THREADS) k_inner(BlkDims d, BlkBuffers b
 
 // --------------------------------------------------------------- apply ----
 template <class T, bool CPLX, int V>
-__global__ void __launch_bounds__(256) k_apply(BlkDims d, BlkBuffers b, int step) {
+__global__ void __launch_bounds__(256) k_apply(BlkDims d, BlkBuffers b, int step, int tile0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int slot = blockIdx.x;
   PairCols pc;
   if (!load_pair(d, b, step, slot, pc)) return;
   if (!b.flags[slot]) return;
   const int tf = (d.mf + TR - 1) / TR, tg = (d.mg + TR - 1) / TR;
-  int tile = blockIdx.y;
+  int tile = tile0 + blockIdx.y;
   T* Y;
   long long ld;
   int m;
@@ -954,9 +954,14 @@ cudaError_t apply_v(const BlkDims& d, const BlkBuffers& b, int step, cudaStream_
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   const int tiles = (d.mf + TR - 1) / TR + (d.mg + TR - 1) / TR + (d.n + TR - 1) / TR;
-  dim3 grid(d.nslots, tiles);
-  kern<<<grid, 256, smem, s>>>(d, b, step);
-  return cudaGetLastError();
+  // tiles of F, G, Z on grid y, in launches of at most 65535 tiles each
+  for (int t0 = 0; t0 < tiles; t0 += 65535) {
+    dim3 grid(d.nslots, std::min(65535, tiles - t0));
+    kern<<<grid, 256, smem, s>>>(d, b, step, t0);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 template <class Ti, class To, bool CPLX, int V>
 cudaError_t inner_v(const BlkDims& d, const BlkBuffers& b, int step, const InnerParams& p, cudaStream_t s) {

@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(32 * oz_gram_warps<V>()) k_gram_oz(BlkDims d, 
 constexpr int ATR = 64;
 
 template <int V, bool CPLX>
-__global__ void __launch_bounds__(256) k_apply_oz(BlkDims d, BlkBuffers b, int step) {
+__global__ void __launch_bounds__(256) k_apply_oz(BlkDims d, BlkBuffers b, int step, int tile0) {
   constexpr int YS = V + 8;  // padded row stride of the Y slices (bf16)
   constexpr int TS = V + 8;  // padded stride of a Z slice column (bf16)
   constexpr int NNW = V / 16;  // column tiles (n8) per warp
@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(256) k_apply_oz(BlkDims d, BlkBuffers b, int s
   if (!load_pair(d, b, step, slot, pc)) return;
   if (!b.flags[slot]) return;
   const int tf = (d.mf + ATR - 1) / ATR, tg = (d.mg + ATR - 1) / ATR;
-  int tile = blockIdx.y;
+  int tile = tile0 + blockIdx.y;
   double* Y;
   long long ld;
   int m;
@@ -753,9 +753,14 @@ static cudaError_t apply_oz_v(const BlkDims& d, const BlkBuffers& b, int step, c
     if (e != cudaSuccess) return e;
   }
   const int tiles = (d.mf + ATR - 1) / ATR + (d.mg + ATR - 1) / ATR + (d.n + ATR - 1) / ATR;
-  dim3 grid(d.nslots, tiles);
-  kern<<<grid, 256, smem, s>>>(d, b, step);
-  return cudaGetLastError();
+  // tiles of F, G, Z on grid y, in launches of at most 65535 tiles each
+  for (int t0 = 0; t0 < tiles; t0 += 65535) {
+    dim3 grid(d.nslots, std::min(65535, tiles - t0));
+    kern<<<grid, 256, smem, s>>>(d, b, step, t0);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_apply_oz(const BlkDims& d, const BlkBuffers& b, bool cplx, int step, cudaStream_t s) {
