@@ -97,7 +97,11 @@ typedef struct {
                                them to their own convergence (or fp32_max_sweeps) */
 } gsvd_config;
 
-/* One problem.  dtype = GSVD_R64 or GSVD_C128. */
+/* One problem.  dtype = GSVD_R64 or GSVD_C128.
+ * Sizes: 1 <= n <= 32768 and n <= m_f, m_g <= 2^30.  n < 4 always runs on the
+ * pointwise kernel, which holds the whole problem in one CTA's shared memory
+ * ((m_f + m_g + n) n doubles, twice that complex, plus its tables, within
+ * 227 KB); a larger problem with n < 4 is GSVD_EINVAL. */
 typedef struct {
   int32_t dtype;
   int32_t reserved;
@@ -194,7 +198,8 @@ int gsvd_poll(gsvd_handle h, uint64_t ticket, gsvd_info *info);
  * call. */
 int gsvd_autotune(gsvd_handle h, int32_t dtype, int64_t m_f, int64_t m_g, int64_t n, int32_t *block_w);
 
-/* Device bytes a solve of this shape needs beyond the caller's buffers. */
+/* Device bytes a solve of this shape needs beyond the caller's buffers; 0 for
+ * a shape the library does not take (see gsvd_problem). */
 uint64_t gsvd_workspace_bytes(const gsvd_config *cfg, int32_t dtype, int64_t m_f, int64_t m_g, int64_t n);
 
 /* Static text of a status code. */

@@ -216,11 +216,16 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// the shapes the library takes: 1 <= n <= 32768, n <= m_F, m_G <= 2^30
+bool shape_ok(int32_t dtype, int64_t mf, int64_t mg, int64_t n) {
+  if (dtype != GSVD_R64 && dtype != GSVD_C128) return false;
+  if (n < 1 || mf < n || mg < n) return false;
+  return n <= 32768 && mf <= (int64_t)1 << 30 && mg <= (int64_t)1 << 30;
+}
+
 int validate(const gsvd_problem* p) {
   if (!p) return GSVD_EINVAL;
-  if (p->dtype != GSVD_R64 && p->dtype != GSVD_C128) return GSVD_EINVAL;
-  if (p->n < 1 || p->m_f < p->n || p->m_g < p->n) return GSVD_EINVAL;
-  if (p->n > 32768 || p->m_f > (int64_t)1 << 30 || p->m_g > (int64_t)1 << 30) return GSVD_EINVAL;
+  if (!shape_ok(p->dtype, p->m_f, p->m_g, p->n)) return GSVD_EINVAL;
   if (p->ldf < p->m_f || p->ldg < p->m_g || p->ldz < p->n) return GSVD_EINVAL;
   if (!p->F || !p->G || !p->Z || !p->sigma_f || !p->sigma_g || !p->sigma) return GSVD_EINVAL;
   if (p->X && (p->dtype != GSVD_R64 || p->ldx < p->n)) return GSVD_EINVAL;
@@ -1040,7 +1045,7 @@ uint64_t gsvd_workspace_bytes(const gsvd_config* cfg, int32_t dtype, int64_t mf,
   else
     gsvd_config_default(&c);
   Plan P;
-  if (!make_plan(c, dtype, mf, mg, n, P)) return 0;
+  if (!shape_ok(dtype, mf, mg, n) || !make_plan(c, dtype, mf, mg, n, P)) return 0;
   return solve_bytes(c, P, mf, mg, n);
 }
 

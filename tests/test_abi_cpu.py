@@ -142,6 +142,18 @@ def test_workspace_bytes_grows_with_size(lib):
     assert prod <= extra <= prod + 4 * (m + n) + 2048 and extra < 2 * 7 * 2 * n * m
 
 
+def test_size_limits_of_the_header(lib):
+    """gsvd.h: n < 4 runs on the pointwise kernel, whose shared memory holds
+    the whole problem; a tall problem with n < 4 has no plan (workspace 0,
+    the solve returns EINVAL), a short one does."""
+    import paper_1909_00101_gb300 as hz
+    cfg = hz.make_config()
+    assert lib.gsvd_workspace_bytes(ctypes.byref(cfg), 0, 100, 100, 2) > 0
+    assert lib.gsvd_workspace_bytes(ctypes.byref(cfg), 0, 100000, 100000, 2) == 0
+    assert lib.gsvd_workspace_bytes(ctypes.byref(cfg), 0, 100000, 100000, 4) > 0
+    assert lib.gsvd_workspace_bytes(ctypes.byref(cfg), 0, 40000, 40000, 32769) == 0
+
+
 def test_binding_structs_match_the_header(tmp_path):
     """Sizes and field offsets of gsvd_config, gsvd_problem and gsvd_info as
     compiled from include/gsvd.h equal the ctypes mirrors of the binding."""
