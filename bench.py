@@ -97,7 +97,23 @@ class Clocks:
             out["reasons"] = sorted(reasons)
         except Exception:
             pass
+        out["verdict"] = clock_verdict(out)
         return out
+
+
+def clock_verdict(clk: dict) -> str:
+    """The timing rule on the clocks seen in the timed region: a thermal or
+    hardware slowdown, or a median SM clock well below the maximum with no
+    reason given (a clock lock), rejects the number; a power cap is kept."""
+    bad = [r for r in clk.get("reasons", []) if r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown")]
+    if bad:
+        return "rejected: " + ", ".join(bad)
+    sm, mx = clk.get("sm_mhz"), clk.get("sm_max_mhz")
+    if sm is None or mx is None:
+        return "unknown: no clock samples"
+    if sm < 0.85 * mx and not clk.get("reasons"):
+        return "rejected: SM clock %.0f of %.0f MHz with no reason" % (sm, mx)
+    return "ok (power cap noted)" if "sw_power_cap" in clk.get("reasons", []) else "ok"
 
 
 def dist_setup(gpus):
