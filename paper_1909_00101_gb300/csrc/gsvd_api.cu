@@ -29,7 +29,6 @@ constexpr double EPS64 = 1.1102230246251565e-16;  // 2^-53
 constexpr double EPS32 = 5.9604644775390625e-08;  // 2^-24
 constexpr int POINTWISE_MAX_N = 64;  // at most 32 pairs per step: one lane each
 constexpr int NCTR = 8;
-constexpr size_t SMEM_LIMIT = 227 * 1024;
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -125,7 +124,7 @@ bool make_plan(const gsvd_config& cfg, int dtype, int64_t mf, int64_t mg, int64_
   const int slots_rr = (int)((n + 1) / 2);
   size_t pw_smem = pointwise_smem_bytes((int)mf, (int)mg, (int)n, P.cplx, false,
                                         cfg.order == GSVD_ORDER_ROW_CYCLIC ? std::max<int64_t>(1, n / 2) : slots_rr);
-  bool pw_ok = n <= POINTWISE_MAX_N && pw_smem <= SMEM_LIMIT;
+  bool pw_ok = n <= POINTWISE_MAX_N && pw_smem <= POINTWISE_SMEM_MAX;
   if (cfg.path == GSVD_PATH_POINTWISE && !pw_ok) return false;
   if (cfg.path == GSVD_PATH_POINTWISE || (cfg.path == GSVD_PATH_AUTO && pw_ok) || n < 4) {
     if (!pw_ok) return false;

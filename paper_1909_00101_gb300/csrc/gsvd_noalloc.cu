@@ -76,7 +76,7 @@ extern "C" int gsvd_solve_small_noalloc(const gsvd_problem* ps, int32_t count, c
   }
   for (int k = 0; k < count; ++k) {
     const gsvd_problem& p = ps[k];
-    if (pointwise_smem_bytes((int)p.m_f, (int)p.m_g, (int)p.n, p.dtype == GSVD_C128, false, slots) > 227 * 1024)
+    if (pointwise_smem_bytes((int)p.m_f, (int)p.m_g, (int)p.n, p.dtype == GSVD_C128, false, slots) > POINTWISE_SMEM_MAX)
       return GSVD_ETOOBIG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);

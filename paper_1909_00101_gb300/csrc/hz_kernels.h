@@ -39,6 +39,9 @@ struct PwParams {
 };
 
 size_t pointwise_smem_bytes(int mf, int mg, int n, bool cplx, bool fp32, int slots);
+// largest dynamic shared memory of a pointwise launch: the 227 KB one CTA may
+// use, less room for the kernel's static shared arrays (512 B in the real one)
+constexpr size_t POINTWISE_SMEM_MAX = 227 * 1024 - 1024;
 // slots: the largest number of pairs per step over the batch (shared-memory layout)
 cudaError_t launch_pointwise(const PwProblem* d_probs, int count, int slots, bool cplx, bool fp32, size_t smem,
                              const PwParams& prm, cudaStream_t stream);
