@@ -95,6 +95,11 @@ typedef struct {
                                over) after a sweep in which big transformations number fewer than
                                this many per mille of the pivot pairs examined (default 50); 0 = run
                                them to their own convergence (or fp32_max_sweeps) */
+  int32_t variant;          /* variants of Sec. 2.6 (Table "Variants") besides the criterion: +1 = the
+                               enhanced dot products of App. A, +2 = no prescaling, each pivot pair
+                               rescaled by D-hat (Z-hat = D-hat Z-hat'); with criterion = 2 these are
+                               variants 4-7.  Default 0.  Variants 1-3 run on the pointwise kernel
+                               only: a problem that takes the blocked path is GSVD_EINVAL */
 } gsvd_config;
 
 /* One problem.  dtype = GSVD_R64 or GSVD_C128.

@@ -39,7 +39,7 @@ class Config(ctypes.Structure):
                 ("max_inflight", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("inner_max_sweeps_fp32", ctypes.c_int32), ("shorten", ctypes.c_int32),
                 ("fp32_params", ctypes.c_int32), ("fp64_gemm", ctypes.c_int32),
-                ("fp32_stop_permille", ctypes.c_int32)]
+                ("fp32_stop_permille", ctypes.c_int32), ("variant", ctypes.c_int32)]
 
 
 class Problem(ctypes.Structure):
@@ -113,7 +113,7 @@ def strerror(status: int) -> str:
 def make_config(precision="fp64", block_w=0, max_sweeps=30, inner_max_sweeps=30, criterion=1, sort=True,
                 path="auto", order="round_robin", fp32_max_sweeps=30, hbm_budget_bytes=60 << 30,
                 max_inflight=16, profile=False, inner_max_sweeps_fp32=1, shorten=1,
-                fp32_params=1, fp64_gemm=1, fp32_stop_permille=50) -> Config:
+                fp32_params=1, fp64_gemm=1, fp32_stop_permille=50, variant=0) -> Config:
     c = Config()
     load_library().gsvd_config_default(ctypes.byref(c))
     c.precision = PREC[precision]
@@ -133,6 +133,7 @@ def make_config(precision="fp64", block_w=0, max_sweeps=30, inner_max_sweeps=30,
     c.fp32_params = fp32_params
     c.fp64_gemm = fp64_gemm
     c.fp32_stop_permille = fp32_stop_permille
+    c.variant = variant
     return c
 
 

@@ -143,6 +143,7 @@ bool make_plan(const gsvd_config& cfg, int dtype, int64_t mf, int64_t mg, int64_
     P.total = P.off_status + 256;
     return true;
   }
+  if (cfg.variant != 0) return false;  // variants 1-3: pointwise kernel only
   P.path = GSVD_PATH_BLOCKED;
   P.w = choose_w(cfg, P.cplx, (int)n);
   P.V = blk_vmax(P.w, P.cplx);
@@ -433,6 +434,8 @@ int solve_pointwise(const gsvd_config& cfg, const gsvd_problem* ps, const int* i
   prm.f32cls = false;
   prm.crit2 = cfg.criterion == 2;
   prm.rowcyc = rowcyc;
+  prm.enhanced = (cfg.variant & 1) != 0;
+  prm.dscale = (cfg.variant & 2) != 0;
   // real and complex problems run in separate launches (one kernel each)
   size_t off = 0;
   std::vector<int> pos(count);
@@ -858,6 +861,7 @@ void gsvd_config_default(gsvd_config* c) {
   c->fp32_params = 1;
   c->fp64_gemm = 1;
   c->fp32_stop_permille = 50;
+  c->variant = 0;
 }
 
 int gsvd_create(gsvd_handle* h, const gsvd_config* cfg, void* stream) {
@@ -870,6 +874,7 @@ int gsvd_create(gsvd_handle* h, const gsvd_config* cfg, void* stream) {
     gsvd_config_default(&c->cfg);
   if (c->cfg.max_sweeps < 1 || c->cfg.inner_max_sweeps < 1 || c->cfg.fp32_max_sweeps < 0 ||
       (c->cfg.criterion != 1 && c->cfg.criterion != 2) || c->cfg.max_inflight < 1 ||
+      c->cfg.variant < 0 || c->cfg.variant > 3 ||
       (c->cfg.precision != GSVD_PREC_FP64 && c->cfg.precision != GSVD_PREC_MIXED)) {
     delete c;
     return GSVD_EINVAL;

@@ -57,7 +57,8 @@ extern "C" int gsvd_solve_small_noalloc(const gsvd_problem* ps, int32_t count, c
     c = *cfg;
   else
     gsvd_config_default(&c);
-  if (c.max_sweeps < 1 || (c.criterion != 1 && c.criterion != 2)) return GSVD_EINVAL;
+  if (c.max_sweeps < 1 || (c.criterion != 1 && c.criterion != 2) || c.variant < 0 || c.variant > 3)
+    return GSVD_EINVAL;
   // every problem must be a valid device problem that fits the pointwise kernel
   const bool rowcyc = c.order == GSVD_ORDER_ROW_CYCLIC;
   int slots = 1;
@@ -104,6 +105,8 @@ extern "C" int gsvd_solve_small_noalloc(const gsvd_problem* ps, int32_t count, c
   prm.f32cls = false;
   prm.crit2 = c.criterion == 2;
   prm.rowcyc = rowcyc;
+  prm.enhanced = (c.variant & 1) != 0;
+  prm.dscale = (c.variant & 2) != 0;
   // descriptors: real problems first, then complex (one launch per kind);
   // status records start at zero on every call (the array keeps old contents)
   int nreal = 0;

@@ -36,6 +36,9 @@ struct PwParams {
   bool f32cls;
   bool crit2;
   bool rowcyc;  // row-cyclic wavefront order (else round robin)
+  // variants of Sec. 2.6 (Table "Variants"), besides crit2 (C2):
+  bool enhanced = false;  // App. A enhanced dot products (variants 1, 3, 5, 7)
+  bool dscale = false;    // no prescaling; each pivot pair rescaled by D-hat (variants 2, 3, 6, 7)
 };
 
 size_t pointwise_smem_bytes(int mf, int mg, int n, bool cplx, bool fp32, int slots);

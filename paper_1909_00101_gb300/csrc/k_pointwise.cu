@@ -13,6 +13,13 @@
 //      swaps them when sorting asks for it.
 // A sweep is a full cycle of the table; the solve stops after a sweep with no
 // transformation (the pointwise rule of Sec. 2.5) or at the sweep cap.
+//
+// VAR selects the variants of Sec. 2.6 (C2 is a run-time flag): bit 1 the
+// enhanced dot products of App. A (real dots and all norms; complex
+// off-diagonal products stay ordinary, App. A defines none for them), bit 2
+// the D-hat rescaling (no prescaling; per pivot pair A' = D A D, B' = D B D
+// with D_kk = 1/sqrt(b_kk) where b_kk != 1, and Z-hat = D Z-hat'; the sort
+// compares the diagonal of Z-hat'^* A' Z-hat').
 #include "hz_device.cuh"
 #include "hz_kernels.h"
 
@@ -47,10 +54,52 @@ __device__ __forceinline__ bool pw_pair(bool rowcyc, int n, int st, int k, int& 
   return j < n;
 }
 
-template <class T, bool CPLX>
+// App. A: c = RD(a b), d = a b - c >= 0 (exact, one fma); the enhanced dot
+// product is the sum of the c plus the sum of the d
+__device__ __forceinline__ void enh_acc(double& c, double& d, double a, double b) {
+  const double p = __dmul_rd(a, b);
+  c += p;
+  d += fma(a, b, -p);
+}
+
+// App. A, the simpler procedure for ||a||^2 of complex data: one element's
+// term (e + the smaller c) + the larger c, e = d_re + d_im
+__device__ __forceinline__ double enh_abs2(double re, double im) {
+  const double cr = __dmul_rd(re, re), ci = __dmul_rd(im, im);
+  const double e = fma(re, re, -cr) + fma(im, im, -ci);
+  return cr <= ci ? (e + cr) + ci : (e + ci) + cr;
+}
+
+// ||y||^2 of column y (m elements, E scalars each) in shared memory, summed
+// by one warp: ordinary (fma) or enhanced; the result on every lane
+template <class T, bool CPLX, bool ENH>
+__device__ __forceinline__ double col_norm2(const T* y, int m, int lane) {
+  if constexpr (!ENH) {
+    double s = 0.0;
+    for (int r = lane; r < (CPLX ? 2 : 1) * m; r += 32) {
+      const double v = y[r];
+      s = fma(v, v, s);
+    }
+    return warp_sum(s);
+  } else if constexpr (!CPLX) {
+    double c = 0.0, d = 0.0;
+    for (int r = lane; r < m; r += 32) {
+      const double v = y[r];
+      enh_acc(c, d, v, v);
+    }
+    return warp_sum(c) + warp_sum(d);
+  } else {
+    double s = 0.0;
+    for (int r = lane; r < m; r += 32) s += enh_abs2(y[2 * r], y[2 * r + 1]);
+    return warp_sum(s);
+  }
+}
+
+template <class T, bool CPLX, int VAR>
 __global__ void __launch_bounds__(512) k_pointwise(const PwProblem* __restrict__ probs, int table_slots,
                                                    PwParams prm) {
   constexpr int E = PW<T, CPLX>::E;
+  constexpr bool ENH = (VAR & 1) != 0, DSC = (VAR & 2) != 0;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const PwProblem P = probs[blockIdx.x];
   const int n = P.n, mf = P.mf, mg = P.mg;
@@ -66,6 +115,7 @@ __global__ void __launch_bounds__(512) k_pointwise(const PwProblem* __restrict__
   int* ctr = reinterpret_cast<int*>(colnorm + 2 * n);               // nall, nbig, fail, rank scratch...
   int* rank = ctr + 4;
   __shared__ double s_xi[32], s_eta[32];  // chain B of the real parameters
+  __shared__ double s_d[2][32];            // D-hat of each pair of a step (DSC)
 
   // load (convert to T), zero Z
   const double* gF = static_cast<const double*>(P.F);
@@ -82,17 +132,17 @@ __global__ void __launch_bounds__(512) k_pointwise(const PwProblem* __restrict__
   if (threadIdx.x < 4) ctr[threadIdx.x] = 0;
   __syncthreads();
 
-  // prescale: z_j = 1/||g_j|| (variant 0), F0 = F Z0, G0 = G Z0, Z = Z0
+  // prescale: z_j = 1/||g_j||, F0 = F Z0, G0 = G Z0, Z = Z0 (the D-hat
+  // variants start from Z0 = I and only check g_j != 0)
   for (int j = warp; j < n; j += nwarps) {
-    double s = 0.0;
-    for (int r = lane; r < E * mg; r += 32) {
-      const double v = sG[(size_t)j * E * mg + r];
-      s = fma(v, v, s);
-    }
-    s = warp_sum(s);
+    double s = col_norm2<T, CPLX, ENH>(sG + (size_t)j * E * mg, mg, lane);
     if (!(s > 0.0)) {
       if (lane == 0) atomicOr(&ctr[2], 1);
       s = 1.0;
+    }
+    if constexpr (DSC) {
+      if (lane == 0) sZ[(size_t)j * E * n + E * j] = T(1);
+      continue;
     }
     const double zj = 1.0 / sqrt(s);
     for (int r = lane; r < E * mf; r += 32) sF[(size_t)j * E * mf + r] = static_cast<T>(sF[(size_t)j * E * mf + r] * zj);
@@ -125,7 +175,21 @@ __global__ void __launch_bounds__(512) k_pointwise(const PwProblem* __restrict__
         if (!pw_pair(prm.rowcyc, n, st, k, i, j)) continue;
         double v[4] = {0.0, 0.0, 0.0, 0.0};
         double w[2] = {0.0, 0.0};
-        if constexpr (!CPLX) {
+        double bii = 1.0, bjj = 1.0;  // DSC: ||g_i||^2, ||g_j||^2
+        if constexpr (!CPLX && ENH) {
+          double dd[4] = {0.0, 0.0, 0.0, 0.0};
+          for (int r = lane; r < mf; r += 32) {
+            const double fi = sF[(size_t)i * mf + r], fj = sF[(size_t)j * mf + r];
+            enh_acc(v[0], dd[0], fi, fi);
+            enh_acc(v[1], dd[1], fj, fj);
+            enh_acc(v[2], dd[2], fi, fj);
+          }
+          for (int r = lane; r < mg; r += 32) enh_acc(v[3], dd[3], (double)sG[(size_t)i * mg + r], (double)sG[(size_t)j * mg + r]);
+          warp_sum4(v);
+          warp_sum4(dd);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) v[q] += dd[q];
+        } else if constexpr (!CPLX) {
           for (int r = lane; r < mf; r += 32) {
             const double fi = sF[(size_t)i * mf + r], fj = sF[(size_t)j * mf + r];
             v[0] = fma(fi, fi, v[0]);
@@ -134,6 +198,25 @@ __global__ void __launch_bounds__(512) k_pointwise(const PwProblem* __restrict__
           }
           for (int r = lane; r < mg; r += 32) v[3] = fma((double)sG[(size_t)i * mg + r], (double)sG[(size_t)j * mg + r], v[3]);
           warp_sum4(v);
+        } else if constexpr (ENH) {
+          // the norms enhanced; Re, Im of conj(f_i) f_j and b_ij ordinary
+          for (int r = lane; r < mf; r += 32) {
+            const double fir = sF[(size_t)i * 2 * mf + 2 * r], fii = sF[(size_t)i * 2 * mf + 2 * r + 1];
+            const double fjr = sF[(size_t)j * 2 * mf + 2 * r], fji = sF[(size_t)j * 2 * mf + 2 * r + 1];
+            v[0] += enh_abs2(fir, fii);
+            v[1] += enh_abs2(fjr, fji);
+            v[2] = fma(fir, fjr, fma(fii, fji, v[2]));
+            v[3] = fma(fir, fji, fma(-fii, fjr, v[3]));
+          }
+          for (int r = lane; r < mg; r += 32) {
+            const double gir = sG[(size_t)i * 2 * mg + 2 * r], gii = sG[(size_t)i * 2 * mg + 2 * r + 1];
+            const double gjr = sG[(size_t)j * 2 * mg + 2 * r], gji = sG[(size_t)j * 2 * mg + 2 * r + 1];
+            w[0] = fma(gir, gjr, fma(gii, gji, w[0]));
+            w[1] = fma(gir, gji, fma(-gii, gjr, w[1]));
+          }
+          warp_sum4(v);
+          w[0] = warp_sum(w[0]);
+          w[1] = warp_sum(w[1]);
         } else {
           for (int r = lane; r < mf; r += 32) {
             const double fir = sF[(size_t)i * 2 * mf + 2 * r], fii = sF[(size_t)i * 2 * mf + 2 * r + 1];
@@ -153,11 +236,33 @@ __global__ void __launch_bounds__(512) k_pointwise(const PwProblem* __restrict__
           w[0] = warp_sum(w[0]);
           w[1] = warp_sum(w[1]);
         }
+        if constexpr (DSC) {
+          bii = col_norm2<T, CPLX, ENH>(sG + (size_t)i * E * mg, mg, lane);
+          bjj = col_norm2<T, CPLX, ENH>(sG + (size_t)j * E * mg, mg, lane);
+        }
         if (lane == 0) {
           PivIn p;
           p.a11 = v[0]; p.a22 = v[1]; p.ar = v[2];
           if constexpr (CPLX) { p.ai = v[3]; p.br = w[0]; p.bi = w[1]; }
           else { p.ai = 0.0; p.br = v[3]; p.bi = 0.0; }
+          if constexpr (DSC) {
+            // A' = D A D, B' = D B D: the diagonal of A' by a division by
+            // b_kk, the off-diagonals times D_kk, where b_kk != 1
+            double d1 = 1.0, d2 = 1.0;
+            if (!(bii > 0.0) || !(bjj > 0.0)) atomicOr(&ctr[2], 1);
+            if (bii != 1.0) {
+              p.a11 = p.a11 / bii;
+              d1 = 1.0 / sqrt(bii);
+              p.ar *= d1; p.ai *= d1; p.br *= d1; p.bi *= d1;
+            }
+            if (bjj != 1.0) {
+              p.a22 = p.a22 / bjj;
+              d2 = 1.0 / sqrt(bjj);
+              p.ar *= d2; p.ai *= d2; p.br *= d2; p.bi *= d2;
+            }
+            s_d[0][k] = d1;
+            s_d[1][k] = d2;
+          }
           pin[k] = p;
         }
       }
@@ -201,6 +306,13 @@ __global__ void __launch_bounds__(512) k_pointwise(const PwProblem* __restrict__
         }
         if (warp == 0) {
           if (have) {
+            if constexpr (DSC) {
+              if (o.flags & PV_ROT) {  // Z-hat = D Z-hat': rows times D11, D22
+                const double d1 = s_d[0][k], d2 = s_d[1][k];
+                o.z11 *= d1; o.z12 *= d1; o.z12i *= d1;
+                o.z21 *= d2; o.z21i *= d2; o.z22 *= d2;
+              }
+            }
             pout[k] = o;
             fl = o.flags;
           }
@@ -274,11 +386,8 @@ __global__ void __launch_bounds__(512) k_pointwise(const PwProblem* __restrict__
 
   // final rescaling (Sec. 2.4): column norms of F and G
   for (int j = warp; j < n; j += nwarps) {
-    double sf = 0.0, sg = 0.0;
-    for (int r = lane; r < E * mf; r += 32) { const double v = sF[(size_t)j * E * mf + r]; sf = fma(v, v, sf); }
-    for (int r = lane; r < E * mg; r += 32) { const double v = sG[(size_t)j * E * mg + r]; sg = fma(v, v, sg); }
-    sf = warp_sum(sf);
-    sg = warp_sum(sg);
+    const double sf = col_norm2<T, CPLX, ENH>(sF + (size_t)j * E * mf, mf, lane);
+    const double sg = col_norm2<T, CPLX, ENH>(sG + (size_t)j * E * mg, mg, lane);
     if (lane == 0) { colnorm[j] = sqrt(sf); colnorm[n + j] = sqrt(sg); }
   }
   __syncthreads();
@@ -334,14 +443,19 @@ size_t pointwise_smem_bytes(int mf, int mg, int n, bool cplx, bool fp32, int slo
   return b;
 }
 
+using Kern = void (*)(const PwProblem*, int, PwParams);
+template <int VAR>
+Kern pick(bool cplx, bool fp32) {
+  if (cplx) return fp32 ? k_pointwise<float, true, VAR> : k_pointwise<double, true, VAR>;
+  return fp32 ? k_pointwise<float, false, VAR> : k_pointwise<double, false, VAR>;
+}
+
 cudaError_t launch_pointwise(const PwProblem* d_probs, int count, int slots, bool cplx, bool fp32, size_t smem,
                              const PwParams& prm, cudaStream_t stream) {
   const int threads = slots >= 16 ? 512 : (slots >= 8 ? 256 : 128);
-  void (*kern)(const PwProblem*, int, PwParams);
-  if (cplx)
-    kern = fp32 ? k_pointwise<float, true> : k_pointwise<double, true>;
-  else
-    kern = fp32 ? k_pointwise<float, false> : k_pointwise<double, false>;
+  const int var = (prm.enhanced ? 1 : 0) | (prm.dscale ? 2 : 0);
+  const Kern kern = var == 0 ? pick<0>(cplx, fp32)
+                             : var == 1 ? pick<1>(cplx, fp32) : var == 2 ? pick<2>(cplx, fp32) : pick<3>(cplx, fp32);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<count, threads, smem, stream>>>(d_probs, slots, prm);

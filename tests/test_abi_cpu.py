@@ -44,10 +44,10 @@ def test_config_defaults(lib):
     assert c.max_sweeps == 30 and c.inner_max_sweeps == 30 and c.criterion == 1 and c.sort == 1
     assert c.hbm_budget_bytes == 60 << 30 and c.precision == 0
     assert c.shorten == 1 and c.fp32_params == 1 and c.inner_max_sweeps_fp32 == 1
-    assert c.fp64_gemm == 1 and c.fp32_stop_permille == 50
-    # the binding's Config mirrors the C struct: fp32_stop_permille is its
-    # last field (the struct is padded to 8 bytes by its uint64 member)
-    assert ctypes.sizeof(hz.Config) == (hz.Config.fp32_stop_permille.offset + 4 + 7) // 8 * 8
+    assert c.fp64_gemm == 1 and c.fp32_stop_permille == 50 and c.variant == 0
+    # the binding's Config mirrors the C struct: variant is its last field
+    # (the struct is padded to 8 bytes by its uint64 member)
+    assert ctypes.sizeof(hz.Config) == (hz.Config.variant.offset + 4 + 7) // 8 * 8
 
 
 def test_strerror(lib):
@@ -101,7 +101,8 @@ def test_invalid_problems_rejected_before_any_launch(lib):
 def test_bad_config_rejected(lib):
     import paper_1909_00101_gb300 as hz
     h = ctypes.c_void_p()
-    for field, val in (("criterion", 3), ("max_sweeps", 0), ("inner_max_sweeps", 0), ("precision", 5)):
+    for field, val in (("criterion", 3), ("max_sweeps", 0), ("inner_max_sweeps", 0), ("precision", 5),
+                       ("variant", 4), ("variant", -1)):
         cfg = hz.make_config()
         setattr(cfg, field, val)
         assert lib.gsvd_create(ctypes.byref(h), ctypes.byref(cfg), None) == hz.EINVAL
@@ -152,6 +153,19 @@ def test_size_limits_of_the_header(lib):
     assert lib.gsvd_workspace_bytes(ctypes.byref(cfg), 0, 100000, 100000, 2) == 0
     assert lib.gsvd_workspace_bytes(ctypes.byref(cfg), 0, 100000, 100000, 4) > 0
     assert lib.gsvd_workspace_bytes(ctypes.byref(cfg), 0, 40000, 40000, 32769) == 0
+
+
+def test_variants_plan_on_the_pointwise_kernel_only(lib):
+    """Variants 1-3 of Sec. 2.6 (enhanced dots, D-hat rescaling) have a plan on
+    the pointwise kernel and none on the blocked path."""
+    import paper_1909_00101_gb300 as hz
+    for v in (1, 2, 3):
+        cfg = hz.make_config(variant=v)
+        assert lib.gsvd_workspace_bytes(ctypes.byref(cfg), 0, 64, 48, 32) > 0
+        assert lib.gsvd_workspace_bytes(ctypes.byref(cfg), 1, 48, 40, 24) > 0
+        assert lib.gsvd_workspace_bytes(ctypes.byref(cfg), 0, 4096, 4096, 2048) == 0
+        blk = hz.make_config(variant=v, path="blocked")
+        assert lib.gsvd_workspace_bytes(ctypes.byref(blk), 0, 64, 48, 32) == 0
 
 
 def test_binding_structs_match_the_header(tmp_path):
