@@ -315,6 +315,28 @@ struct KTimer {
     ev.clear();
     kind.clear();
   }
+  KTimer() = default;
+  KTimer(const KTimer&) = delete;
+  KTimer& operator=(const KTimer&) = delete;
+  ~KTimer() {
+    for (auto e : ev) cudaEventDestroy(e);  // events of a solve that ended early
+  }
+};
+
+// the three timing events of one solve, destroyed on every return path
+struct SolveEvents {
+  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+  SolveEvents() {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventCreate(&e2);
+  }
+  ~SolveEvents() {
+    for (cudaEvent_t e : {e0, e1, e2})
+      if (e) cudaEventDestroy(e);
+  }
+  SolveEvents(const SolveEvents&) = delete;
+  SolveEvents& operator=(const SolveEvents&) = delete;
 };
 
 int run_sweeps(const Plan& P, const gsvd_config& cfg, bool fp32, void* F, long long ldf, void* G, long long ldg,
@@ -515,10 +537,8 @@ int solve_plain(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info, 
   if (!make_plan(cfg, p->dtype, p->m_f, p->m_g, p->n, P)) return GSVD_EINVAL;
   CK(ws.ensure(P.total));
   unsigned char* w = static_cast<unsigned char*>(ws.p);
-  cudaEvent_t e0, e1, e2;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  cudaEventCreate(&e2);
+  SolveEvents ev;
+  cudaEvent_t e0 = ev.e0, e1 = ev.e1, e2 = ev.e2;
   cudaEventRecord(e0, s);
   int* d_status = reinterpret_cast<int*>(w + P.off_status);
   CK(cudaMemsetAsync(d_status, 0, 16, s));
@@ -596,9 +616,6 @@ int solve_plain(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info, 
     cudaEventElapsedTime(&ms_32, e0, e1);
     cudaEventElapsedTime(&ms_64, e1, e2);
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  cudaEventDestroy(e2);
   info->t_total_us = ms_all * 1e3;
   info->t_fp32_us = cfg.precision == GSVD_PREC_MIXED ? ms_32 * 1e3 : 0.0;
   info->t_refine_us = cfg.precision == GSVD_PREC_MIXED ? ms_64 * 1e3 : 0.0;
