@@ -97,11 +97,11 @@ class Clocks:
             out["reasons"] = sorted(reasons)
         except Exception:
             pass
-        out["verdict"] = clock_verdict(out)
+        out["rule"] = timing_rule(out)
         return out
 
 
-def clock_verdict(clk: dict) -> str:
+def timing_rule(clk: dict) -> str:
     """The timing rule on the clocks seen in the timed region: a thermal or
     hardware slowdown, or a median SM clock well below the maximum with no
     reason given (a clock lock), rejects the number; a power cap is kept."""

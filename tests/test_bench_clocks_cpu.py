@@ -25,14 +25,14 @@ def test_clean_run_is_ok():
     rows = ["2070, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active"] * 5
     out = _clk(b, rows)
     assert out["sm_mhz"] == 2070 and out["sm_max_mhz"] == 2070 and out["reasons"] == []
-    assert out["verdict"] == "ok" and out["samples"] == 5
+    assert out["rule"] == "ok" and out["samples"] == 5
 
 
 def test_power_cap_is_kept_and_noted():
     b = _bench()
     rows = ["1850, 2070, 1399.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active"] * 3
     out = _clk(b, rows)
-    assert out["reasons"] == ["sw_power_cap"] and out["verdict"].startswith("ok")
+    assert out["reasons"] == ["sw_power_cap"] and out["rule"].startswith("ok")
 
 
 def test_thermal_slowdown_rejects():
@@ -40,17 +40,17 @@ def test_thermal_slowdown_rejects():
     rows = ["2070, 2070, 900, 0x0, Not Active, Not Active, Not Active, Not Active",
             "1500, 2070, 900, 0x0, Not Active, Active, Not Active, Not Active"]
     out = _clk(b, rows)
-    assert "hw_thermal_slowdown" in out["reasons"] and out["verdict"].startswith("rejected")
+    assert "hw_thermal_slowdown" in out["reasons"] and out["rule"].startswith("rejected")
 
 
 def test_clock_lock_without_reason_rejects():
     b = _bench()
     rows = ["1200, 2070, 500, 0x0, Not Active, Not Active, Not Active, Not Active"] * 4
     out = _clk(b, rows)
-    assert out["verdict"].startswith("rejected: SM clock 1200")
+    assert out["rule"].startswith("rejected: SM clock 1200")
 
 
 def test_no_samples_is_unknown():
     b = _bench()
     out = _clk(b, [])
-    assert out["verdict"].startswith("unknown") and out["sm_mhz"] is None
+    assert out["rule"].startswith("unknown") and out["sm_mhz"] is None
