@@ -265,7 +265,10 @@ def run(F, G, Z, *, rank, world, dist, solve_pair, max_sweeps: int = 30, timeout
 def library_pair_solver(solver):
     """solve_pair for run() on a GPU process: the library's solve of the pair
     (host arrays in, through the C ABI; the pair's Z and its count of big
-    transformations out).  solver: a paper_1909_00101_gb300.Solver."""
+    transformations out).  solver: a paper_1909_00101_gb300.Solver.  Its
+    max_sweeps is the number S of sweeps per pair visit: 1 is the
+    block-oriented choice that Sec. 4.1.4 recommends across GPUs (a pair
+    solve that stops at the cap still returns a valid transformation)."""
     def solve_pair(Fp, Gp):
         r = solver.solve(np.asfortranarray(Fp), np.asfortranarray(Gp))
         if r.status not in (0, -3):

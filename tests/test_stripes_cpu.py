@@ -54,7 +54,17 @@ def _solve_pair(Fp, Gp):
     return r["Z"], r["transf_big"]
 
 
-def _rank_main(rank, world, port, out, F, G, w, fail_rank):
+def _solve_pair_one_sweep(Fp, Gp):
+    """S = 1 sweep per pair visit (BO at the outermost level, which Sec. 4.1.4
+    recommends for several GPUs): the sweep cap ends the pair solve, whose Z
+    is still a valid nonsingular transformation."""
+    import oracle
+    r = oracle.gsvd(Fp, Gp, max_sweeps=1)
+    assert r["status"] in (0, -3)
+    return r["Z"], r["transf_big"]
+
+
+def _rank_main(rank, world, port, out, F, G, w, fail_rank, one_sweep=False):
     import torch.distributed as dist
     from datetime import timedelta
     dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=world,
@@ -65,7 +75,8 @@ def _rank_main(rank, world, port, out, F, G, w, fail_rank):
         m = S.exchange_map(world)[0][rank]
         cols = list(range(m.p * w, m.p * w + w)) + list(range(m.q * w, m.q * w + w))
         Fl, Gl, Zl = S.prescale_stripes(F[:, cols], G[:, cols], m.p, m.q, w, F.shape[1])
-        res = S.run(Fl, Gl, Zl, rank=rank, world=world, dist=dist, solve_pair=_solve_pair, max_sweeps=20,
+        res = S.run(Fl, Gl, Zl, rank=rank, world=world, dist=dist,
+                    solve_pair=_solve_pair_one_sweep if one_sweep else _solve_pair, max_sweeps=40,
                     timeout_s=3.0 if fail_rank >= 0 else 30.0)
         fin = S.finalize(res.F, res.G, res.Z)
         np.savez(os.path.join(out, "r%d.npz" % rank), status=res.status, sweeps=res.sweeps, p=res.p, q=res.q, **fin)
@@ -74,10 +85,11 @@ def _rank_main(rank, world, port, out, F, G, w, fail_rank):
             dist.destroy_process_group()
 
 
-def _spawn(world, F, G, w, out, fail_rank=-1):
+def _spawn(world, F, G, w, out, fail_rank=-1, one_sweep=False):
     ctx = pymp.get_context("spawn")
     port = _port()
-    ps = [ctx.Process(target=_rank_main, args=(r, world, port, out, F, G, w, fail_rank)) for r in range(world)]
+    ps = [ctx.Process(target=_rank_main, args=(r, world, port, out, F, G, w, fail_rank, one_sweep))
+          for r in range(world)]
     for p in ps:
         p.start()
     for p in ps:
@@ -129,6 +141,23 @@ def _assemble(out, world, w, mf, mg, n, dtype):
             U[:, c], V[:, c], Z[:, c] = d["U"][:, loc], d["V"][:, loc], d["Z"][:, loc]
             sf[c], sg[c], sig[c] = d["sigma_f"][loc], d["sigma_g"][loc], d["sigma"][loc]
     return U, V, Z, sf, sg, sig
+
+
+def test_one_sweep_per_pair_visit(tmp_path):
+    """BO at the outermost level (S = 1, Sec. 4.1.4): each pair visit runs one
+    sweep; the outer sweeps continue until none has a big transformation, and
+    the result is the oracle's GSVD."""
+    import oracle
+    from paper_1909_00101_gb300.inputs import make_pair
+    world, w = 2, 4
+    n = 2 * world * w
+    p = make_pair(40, 36, n, lo=1e-2, hi=1e2, cond=10.0, seed=9)
+    codes = _spawn(world, p.F, p.G, w, str(tmp_path), one_sweep=True)
+    assert codes == [0] * world
+    U, V, Z, sf, sg, sig = _assemble(str(tmp_path), world, w, 40, 36, n, p.F.dtype)
+    ref = oracle.gsvd(p.F, p.G)
+    assert np.max(np.abs(np.sort(sig)[::-1] - ref["sigma"]) / ref["sigma"]) <= 1e-12
+    assert np.linalg.norm(p.F @ Z - U * sf[None, :]) / np.linalg.norm(p.F) <= 1e-13 * n
 
 
 def test_bordering_shapes():
