@@ -66,6 +66,24 @@ def make_pair(mf: int, mg: int, n: int, *, lo: float = 1e-2, hi: float = 1e2,
     return Pair(F=F, G=G, sigma=np.sort(sig)[::-1].copy(), cond_x=float(cond), seed=seed)
 
 
+def make_graded_pair(mf: int, mg: int, n: int, kappa_b_exp: float, *, seed: int = 0) -> tuple:
+    """A pair in the manner of the GSVD-versus-GEVD experiment of App. G:
+    A = F^T F with cond(A) = 10 (F = U0 diag(f) Q with f log-spaced in
+    [1, sqrt(10)]) and G = V0 C diag(d) with C well conditioned (cond 2) and
+    d log-spaced in [10^(-kappa_b_exp / 2), 1] in a seeded order, so that
+    cond(B) = cond(G^T G) is about 10^kappa_b_exp through the column scaling
+    of G alone.  Real float64, column-major; the reference sigma of the
+    rounded pair is to be computed, not generated."""
+    rng = np.random.default_rng(seed)
+    f = np.logspace(0.0, 0.5, n)
+    F = (_haar(rng, mf, n, False) * f[None, :]) @ _haar(rng, n, n, False)
+    c = np.logspace(0.0, np.log10(2.0), n)
+    C = (_haar(rng, n, n, False) * c[None, :]) @ _haar(rng, n, n, False)
+    d = np.logspace(0.0, -kappa_b_exp / 2.0, n)[rng.permutation(n)]
+    G = (_haar(rng, mg, n, False) @ C) * d[None, :]
+    return np.asfortranarray(F), np.asfortranarray(G)
+
+
 def batch_shapes(count: int, *, n_lo: int = 16, n_hi: int = 256, seed: int = 0):
     """Shapes (mF, mG, n) of a batch: n log-uniform in [n_lo, n_hi], mF, mG uniform in [n, 2n]."""
     rng = np.random.default_rng(seed)
