@@ -18,10 +18,23 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/gsvd.h"
 #include "hz_kernels.h"
 
 using namespace hz;
+
+namespace {
+// a named host range around one phase of a solve, for profilers that record
+// NVTX ranges (a no-op when none is attached)
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
+}  // namespace
 
 namespace {
 
@@ -343,6 +356,7 @@ int run_sweeps(const Plan& P, const gsvd_config& cfg, bool fp32, void* F, long l
                void* Z, long long ldz, unsigned char* ws, unsigned long long* h_ctr, int max_sweeps,
                cudaStream_t s, int* sweeps_out, uint64_t* tall, uint64_t* tbig, int* chol_skipped,
                gsvd_info* info) {
+  TraceRange phase(fp32 ? "gsvd sweeps fp32" : "gsvd sweeps fp64");
   BlkDims d;
   d.mf = P.mf; d.mg = P.mg; d.n = P.n; d.w = P.w; d.nblk = P.nblk; d.nslots = P.nslots;
   // FP64 sweeps: Gram and apply on the tensor cores (sliced operands) or on
@@ -596,6 +610,7 @@ int solve_plain(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info, 
       status = run_sweeps(P, cfg, false, F, p->ldf, G, p->ldg, Z, p->ldz, w, h_ctr, cfg.max_sweeps, s, &sw64,
                           &tall, &tbig, &chol, info);
     }
+    TraceRange phase_fin("gsvd finalize");
     CK(launch_finalize(P.mf, P.mg, P.n, P.cplx, F, p->ldf, G, p->ldg, Z, p->ldz, p->sigma_f, p->sigma_g, p->sigma,
                        reinterpret_cast<double*>(w + P.off_norms), reinterpret_cast<int*>(w + P.off_rank),
                        reinterpret_cast<double*>(w + P.off_work), d_status, s));
@@ -630,6 +645,7 @@ constexpr int SHORT_SKIP = 100;
 // with F and G untouched, when a first Cholesky fails (too ill-conditioned).
 int solve_shortened(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info, DevBuf& ws,
                     unsigned long long* h_ctr, cudaStream_t s) {
+  TraceRange phase("gsvd shortened solve");
   const int n = (int)p->n, mf = (int)p->m_f, mg = (int)p->m_g;
   double* F = (double*)p->F;
   double* G = (double*)p->G;
@@ -715,6 +731,7 @@ int solve_shortened(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* in
 
 int solve_device_core(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info, DevBuf& ws,
                       unsigned long long* h_ctr, cudaStream_t s) {
+  TraceRange phase("gsvd solve");
   Plan P;
   if (!make_plan(cfg, p->dtype, p->m_f, p->m_g, p->n, P)) return GSVD_EINVAL;
   if (shorten_applies(cfg, P, p->m_f, p->m_g, p->n)) {
