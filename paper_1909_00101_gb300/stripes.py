@@ -18,7 +18,8 @@ process encoded as -(t + 1) when the stripe becomes the target's first stripe
 and t + 1 when it becomes the second.
 
 n not divisible into 2 s stripes of one width is bordered first (border,
-unborder: Sec. 3.1, Sec. 4.1).
+unborder: Sec. 3.1, Sec. 4.1).  solve() runs the whole method for a process
+that holds the full pair and gathers the GSVD on process 0.
 
 This module is host logic only (no arithmetic of the method): the pair solver
 is passed in.  On GPUs it is the library's own solve of the pair; the tests
@@ -286,3 +287,56 @@ def finalize(F: np.ndarray, G: np.ndarray, Z: np.ndarray) -> dict:
     th = 1.0 / np.sqrt(sf * sf + sg * sg)
     return {"U": F / sf[None, :], "V": G / sg[None, :], "Z": Z * th[None, :], "sigma_f": sf * th,
             "sigma_g": sg * th, "sigma": sf / sg}
+
+
+def solve(F: np.ndarray, G: np.ndarray, *, rank: int, world: int, dist, solve_pair, unit: int = 1,
+          max_sweeps: int = 30, timeout_s: float = 30.0):
+    """The whole multi-process GSVD of Sec. 4 for one process that holds the
+    full pair (F, G): bordering (Sec. 3.1, Sec. 4.1) to 2 world stripes of one
+    width (a multiple of unit), this process's two stripes of step 0 with the
+    prescaling of Sec. 3.3, the sweeps (run), the final rescaling of Sec. 3.4
+    on its columns, and a gather to process 0, which removes the bordering
+    and sorts by descending Sigma (stable).  Returns (status, result): on
+    process 0 result is a dict with U, V, Z, sigma_f, sigma_g, sigma and
+    sweeps; elsewhere None.  The status is the worst of the processes'
+    (0 ok, -3 no convergence, -6 a wait timed out)."""
+    mf, n = F.shape
+    mg = G.shape[0]
+    Fb, Gb, k = border(F, G, world, unit=unit)
+    nb = n + k
+    w = nb // (2 * world)
+    m = exchange_map(world)[0][rank]
+    cols = list(range(m.p * w, m.p * w + w)) + list(range(m.q * w, m.q * w + w))
+    Fl, Gl, Zl = prescale_stripes(Fb[:, cols], Gb[:, cols], m.p, m.q, w, nb)
+    res = run(Fl, Gl, Zl, rank=rank, world=world, dist=dist, solve_pair=solve_pair, max_sweeps=max_sweeps,
+              timeout_s=timeout_s)
+    fin = finalize(res.F, res.G, res.Z)
+    part = (res.status, res.sweeps, res.p, res.q, fin)
+    if world == 1:
+        parts = [part]
+    else:
+        parts = [None] * world if rank == 0 else None
+        dist.gather_object(part, parts, dst=0)
+    if rank != 0:
+        return res.status, None
+    status = 0
+    for st, *_ in parts:
+        if st != 0 and (status == 0 or st < status):
+            status = st
+    dt = np.result_type(F.dtype, G.dtype)
+    U = np.zeros((Fb.shape[0], nb), dtype=dt)
+    V = np.zeros((Gb.shape[0], nb), dtype=dt)
+    Z = np.zeros((nb, nb), dtype=dt)
+    sf, sg, sig = np.zeros(nb), np.zeros(nb), np.zeros(nb)
+    for _, _, p, q, f in parts:
+        for slot, stripe in ((0, p), (1, q)):
+            c = slice(stripe * w, stripe * w + w)
+            loc = slice(slot * w, slot * w + w)
+            U[:, c], V[:, c], Z[:, c] = f["U"][:, loc], f["V"][:, loc], f["Z"][:, loc]
+            sf[c], sg[c], sig[c] = f["sigma_f"][loc], f["sigma_g"][loc], f["sigma"][loc]
+    if k:
+        U, V, Z, sf, sg, sig = unborder(U, V, Z, sf, sg, sig, mf, mg, n)
+    order = np.argsort(-sig, kind="stable")
+    out = {"U": U[:, order], "V": V[:, order], "Z": Z[:, order], "sigma_f": sf[order], "sigma_g": sg[order],
+           "sigma": sig[order], "sweeps": max(pp[1] for pp in parts)}
+    return status, out

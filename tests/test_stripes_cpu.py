@@ -203,6 +203,44 @@ def test_bordered_ranks_match_the_oracle(tmp_path):
         S.unborder(*bad, 40, 36, 10)
 
 
+def _solve_main(rank, world, port, out, F, G, unit):
+    import torch.distributed as dist
+    from datetime import timedelta
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=world,
+                            timeout=timedelta(seconds=30))
+    try:
+        st, res = S.solve(F, G, rank=rank, world=world, dist=dist, solve_pair=_solve_pair, unit=unit)
+        if rank == 0:
+            np.savez(os.path.join(out, "global.npz"), status=st, **{k: v for k, v in res.items()})
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,n,cplx", [(2, 13, False), (3, 24, False), (2, 11, True)])
+def test_whole_solve_gathered_on_process_zero(tmp_path, world, n, cplx):
+    """S.solve: bordering, the sweeps on every process, and the gathered,
+    unbordered, sorted GSVD on process 0 equal the oracle's."""
+    import oracle
+    from gsvd_checks import invariants
+    from paper_1909_00101_gb300.inputs import make_pair
+    p = make_pair(40, 36, n, lo=1e-2, hi=1e2, cond=10.0, cplx=cplx, seed=n)
+    ctx = pymp.get_context("spawn")
+    port = _port()
+    ps = [ctx.Process(target=_solve_main, args=(r, world, port, str(tmp_path), p.F, p.G, 2)) for r in range(world)]
+    for q in ps:
+        q.start()
+    for q in ps:
+        q.join(120)
+    assert [q.exitcode for q in ps] == [0] * world
+    d = np.load(tmp_path / "global.npz")
+    assert int(d["status"]) == 0 and d["U"].shape == (40, n) and d["Z"].shape == (n, n)
+    ref = oracle.gsvd(p.F, p.G)
+    assert np.max(np.abs(d["sigma"] - ref["sigma"]) / ref["sigma"]) <= 1e-12
+    inv = invariants(p.F, p.G, d["U"], d["V"], d["Z"], d["sigma_f"], d["sigma_g"], d["sigma"])
+    assert inv["FZ"] < 1e-13 * n and inv["GZ"] < 1e-13 * n and inv["UU"] < 1e-12 and inv["VV"] < 1e-12
+    assert inv["sorted"] and inv["scale"] <= 8 * 2.0 ** -53
+
+
 def test_a_failed_rank_ends_the_others_waits(tmp_path):
     from paper_1909_00101_gb300.inputs import make_pair
     world, w = 2, 4
