@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(512) k_pointwise(const PwProblem* __restrict__
   PivIn* pin = reinterpret_cast<PivIn*>(sZ + (size_t)E * n * n);
   PivotOut* pout = reinterpret_cast<PivotOut*>(pin + table_slots);
   double* colnorm = reinterpret_cast<double*>(pout + table_slots);  // 2n: nf, ng
-  int* ctr = reinterpret_cast<int*>(colnorm + 2 * n);               // nall, nbig, fail, rank scratch...
+  int* ctr = reinterpret_cast<int*>(colnorm + 2 * n);               // nall, nbig, fail, overflow
   int* rank = ctr + 4;
   __shared__ double s_xi[32], s_eta[32];  // chain B of the real parameters
   __shared__ double s_d[2][32];            // D-hat of each pair of a step (DSC)
@@ -388,7 +388,11 @@ __global__ void __launch_bounds__(512) k_pointwise(const PwProblem* __restrict__
   for (int j = warp; j < n; j += nwarps) {
     const double sf = col_norm2<T, CPLX, ENH>(sF + (size_t)j * E * mf, mf, lane);
     const double sg = col_norm2<T, CPLX, ENH>(sG + (size_t)j * E * mg, mg, lane);
-    if (lane == 0) { colnorm[j] = sqrt(sf); colnorm[n + j] = sqrt(sg); }
+    if (lane == 0) {
+      colnorm[j] = sqrt(sf);
+      colnorm[n + j] = sqrt(sg);
+      if (!isfinite(sf) || !isfinite(sg) || !(sg > 0.0)) atomicOr(&ctr[3], 1);  // overflow
+    }
   }
   __syncthreads();
   // stable rank by descending sigma = ||f_j|| / ||g_j|| (ties: lower index first)
@@ -426,7 +430,7 @@ __global__ void __launch_bounds__(512) k_pointwise(const PwProblem* __restrict__
     P.sigma[rank[j]] = nf / ng;
   }
   if (threadIdx.x == 0) {
-    P.stats->status = status;
+    P.stats->status = (status == ST_OK && ctr[3]) ? ST_EOVERFLOW : status;
     P.stats->sweeps = sweeps;
     P.stats->transf_all = tall;
     P.stats->transf_big = tbig;
