@@ -23,7 +23,7 @@ that holds the full pair and gathers the GSVD on process 0.
 
 This module is host logic only (no arithmetic of the method): the pair solver
 is passed in.  On GPUs it is the library's own solve of the pair; the tests
-run it on CPU ranks (gloo).  Any process that fails ends the others' waits by
+run it on CPU ranks.  Stripes travel as CPU tensors in a gloo group.  Any process that fails ends the others' waits by
 a timeout, which the driver reports as a status instead of hanging.
 """
 from __future__ import annotations
@@ -187,7 +187,7 @@ def _unwire(t, cplx: bool) -> np.ndarray:
     return np.ascontiguousarray(a).view(np.complex128) if cplx else a
 
 
-def _run(F, G, Z, *, rank, world, dist, solve_pair, max_sweeps=30, timeout_s=30.0) -> StripeResult:
+def _run(F, G, Z, *, rank, world, dist, solve_pair, max_sweeps=30, timeout_s=30.0, group=None) -> StripeResult:
     import torch
     maps = exchange_map(world)
     nsteps = len(maps)
@@ -219,11 +219,11 @@ def _run(F, G, Z, *, rank, world, dist, solve_pair, max_sweeps=30, timeout_s=30.
                 if sr == rank:
                     local_copy[slot] = sl
                 else:
-                    works.append(dist.irecv(inc[slot], src=sr, tag=slot + 1))
+                    works.append(dist.irecv(inc[slot], src=sr, tag=slot + 1, group=group))
             for local, code in enumerate((m.t0, m.t1)):
                 t, slot = decode(code)
                 if t != rank:
-                    works.append(dist.isend(out[local], dst=t, tag=slot + 1))
+                    works.append(dist.isend(out[local], dst=t, tag=slot + 1, group=group))
             for slot, sl in local_copy.items():
                 inc[slot].copy_(out[sl])
             try:
@@ -236,7 +236,7 @@ def _run(F, G, Z, *, rank, world, dist, solve_pair, max_sweeps=30, timeout_s=30.
         tot = torch.tensor([big], dtype=torch.int64)
         try:
             if world > 1:
-                dist.all_reduce(tot, async_op=True).wait(tmo)
+                dist.all_reduce(tot, group=group, async_op=True).wait(tmo)
         except RuntimeError:
             m = maps[0][rank]
             return StripeResult(-6, sweeps, m.p, m.q, buf[:mf], buf[mf:mf + mg], buf[mf + mg:])
@@ -247,20 +247,26 @@ def _run(F, G, Z, *, rank, world, dist, solve_pair, max_sweeps=30, timeout_s=30.
     return StripeResult(-3, sweeps, m.p, m.q, buf[:mf], buf[mf:mf + mg], buf[mf + mg:])
 
 
-def run(F, G, Z, *, rank, world, dist, solve_pair, max_sweeps: int = 30, timeout_s: float = 30.0) -> StripeResult:
+def run(F, G, Z, *, rank, world, dist, solve_pair, max_sweeps: int = 30, timeout_s: float = 30.0,
+        group=None) -> StripeResult:
     """The sweeps of Sec. 4.2 for this process.
 
     F (m_F x 2w), G (m_G x 2w), Z (n x 2w): this process's two stripes of
     step 0 (its pair in exchange_map(world)[0][rank]), prescaled
     (prescale_stripes).  solve_pair(Fpq, Gpq) -> (Zpq, big): a nonsingular
     transformation of the pair and its count of big transformations.  dist:
-    torch.distributed with an initialised process group.  A wait that runs
+    torch.distributed with an initialised process group; group: the group
+    the stripes travel in (None = the default one).  The stripes are host
+    arrays and travel as CPU tensors, between host buffers as the paper's
+    CPU stripes do, so the group's backend must move CPU tensors (gloo; on
+    GPU processes whose default group is NCCL, pass a gloo group made with
+    dist.new_group(backend="gloo")).  A wait that runs
     out of time (a failed peer) gives status -6; no convergence in
     max_sweeps gives -3.  At the end every process holds the stripes of step
     0 again (the map wraps around after each sweep).
     """
     return _run(F, G, Z, rank=rank, world=world, dist=dist, solve_pair=solve_pair, max_sweeps=max_sweeps,
-                timeout_s=timeout_s)
+                timeout_s=timeout_s, group=group)
 
 
 def library_pair_solver(solver):
@@ -290,7 +296,7 @@ def finalize(F: np.ndarray, G: np.ndarray, Z: np.ndarray) -> dict:
 
 
 def solve(F: np.ndarray, G: np.ndarray, *, rank: int, world: int, dist, solve_pair, unit: int = 1,
-          max_sweeps: int = 30, timeout_s: float = 30.0):
+          max_sweeps: int = 30, timeout_s: float = 30.0, group=None):
     """The whole multi-process GSVD of Sec. 4 for one process that holds the
     full pair (F, G): bordering (Sec. 3.1, Sec. 4.1) to 2 world stripes of one
     width (a multiple of unit), this process's two stripes of step 0 with the
@@ -309,14 +315,14 @@ def solve(F: np.ndarray, G: np.ndarray, *, rank: int, world: int, dist, solve_pa
     cols = list(range(m.p * w, m.p * w + w)) + list(range(m.q * w, m.q * w + w))
     Fl, Gl, Zl = prescale_stripes(Fb[:, cols], Gb[:, cols], m.p, m.q, w, nb)
     res = run(Fl, Gl, Zl, rank=rank, world=world, dist=dist, solve_pair=solve_pair, max_sweeps=max_sweeps,
-              timeout_s=timeout_s)
+              timeout_s=timeout_s, group=group)
     fin = finalize(res.F, res.G, res.Z)
     part = (res.status, res.sweeps, res.p, res.q, fin)
     if world == 1:
         parts = [part]
     else:
         parts = [None] * world if rank == 0 else None
-        dist.gather_object(part, parts, dst=0)
+        dist.gather_object(part, parts, dst=0, group=group)
     if rank != 0:
         return res.status, None
     status = 0

@@ -209,7 +209,8 @@ def _solve_main(rank, world, port, out, F, G, unit):
     dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=world,
                             timeout=timedelta(seconds=30))
     try:
-        st, res = S.solve(F, G, rank=rank, world=world, dist=dist, solve_pair=_solve_pair, unit=unit)
+        grp = dist.new_group(backend="gloo")   # the stripes' own group, as on NCCL processes
+        st, res = S.solve(F, G, rank=rank, world=world, dist=dist, solve_pair=_solve_pair, unit=unit, group=grp)
         if rank == 0:
             np.savez(os.path.join(out, "global.npz"), status=st, **{k: v for k, v in res.items()})
     finally:
