@@ -242,6 +242,18 @@ def test_whole_solve_gathered_on_process_zero(tmp_path, world, n, cplx):
     assert inv["sorted"] and inv["scale"] <= 8 * 2.0 ** -53
 
 
+def test_single_process_solve_needs_no_process_group():
+    """world = 1: two stripes on one process, exchanged locally; no
+    torch.distributed calls, and the result is the oracle's GSVD."""
+    import oracle
+    from paper_1909_00101_gb300.inputs import make_pair
+    p = make_pair(30, 26, 9, seed=21)
+    st, res = S.solve(p.F, p.G, rank=0, world=1, dist=None, solve_pair=_solve_pair)
+    ref = oracle.gsvd(p.F, p.G)
+    assert st == 0 and res["U"].shape == (30, 9)
+    assert np.max(np.abs(res["sigma"] - ref["sigma"]) / ref["sigma"]) <= 1e-12
+
+
 def test_a_failed_rank_ends_the_others_waits(tmp_path):
     from paper_1909_00101_gb300.inputs import make_pair
     world, w = 2, 4
