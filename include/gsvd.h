@@ -224,7 +224,8 @@ const char *gsvd_strerror(int status);
  * the process exits.  Limits: count <= GSVD_NOALLOC_MAX_PROBLEMS and n <= 64
  * with F, G, Z fitting in shared memory (else GSVD_ETOOBIG); every pointer of
  * every problem must be device memory (else GSVD_EINVAL).  cfg may be NULL
- * (defaults; precision, path and block width are ignored: FP64 pointwise).
+ * (defaults; precision, path and block width are ignored: FP64 pointwise;
+ * criterion, sort, order, max_sweeps and variant apply).
  * cuda_stream: a cudaStream_t of the current device, NULL = legacy stream.
  *
  * The first call on a device (with that device current) looks up the array's
