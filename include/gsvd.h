@@ -16,9 +16,10 @@
  * Real data is double; complex data is interleaved (re, im) doubles, the layout
  * of C99 double _Complex and of numpy/torch complex128.  F is overwritten by U
  * and G by V (in place, as in Sec. 3.1.1); Z (n x n) and the three length-n
- * vectors are outputs.  Pointers may be device pointers (the solve runs in
- * place) or host pointers (pageable or pinned: the library copies in and out
- * through its own device buffers); one problem must not mix the two.
+ * vectors are outputs.  Pointers may be device pointers of the current device
+ * (the solve runs in place) or host pointers (pageable or pinned: the library
+ * copies in and out through its own device buffers); one problem must not mix
+ * the two, and memory of another device is GSVD_EINVAL.
  *
  * Ownership: the caller owns every buffer passed in a gsvd_problem; the
  * library owns the handle, its stream use, device workspace and the serving
@@ -222,18 +223,23 @@ const char *gsvd_strerror(int status);
  * it reads and the status records it writes) is a fixed array of about 480 KiB
  * compiled into the library, which every GPU that loads the library keeps until
  * the process exits.  Limits: count <= GSVD_NOALLOC_MAX_PROBLEMS and n <= 64
- * with F, G, Z fitting in shared memory (else GSVD_ETOOBIG); every pointer of
- * every problem must be device memory (else GSVD_EINVAL).  cfg may be NULL
+ * with F, G, Z fitting in shared memory (else GSVD_ETOOBIG); m_F, m_G <= 2^30
+ * as for gsvd_solve; every pointer of every problem must be memory of the
+ * current device or managed memory (else GSVD_EINVAL).  cfg may be NULL
  * (defaults; precision, path and block width are ignored: FP64 pointwise;
  * criterion, sort, order, max_sweeps and variant apply).
  * cuda_stream: a cudaStream_t of the current device, NULL = legacy stream.
  *
  * The first call on a device (with that device current) looks up the array's
- * device address; make that first call before any stream capture.  Every call
- * reuses the same array, so calls are serialized inside the library: two
- * calls on the same device whose work overlapped on the GPU would race on it.
+ * device address; make that first call before any stream capture.  The call
+ * is synchronous: it returns after its work on cuda_stream has finished.
+ * Every call reuses the same array, and the array keeps the last call's
+ * contents (the status records are cleared at the start of each call); calls
+ * are serialized inside the library, and two calls on the same device whose
+ * work overlapped on the GPU would race on the array.
  * Returns GSVD_OK if every problem succeeded, else the first failing status;
- * infos (may be NULL) receives one report per problem. */
+ * infos (may be NULL) receives one report per problem.  An argument rejection
+ * (GSVD_EINVAL or GSVD_ETOOBIG before any launch) leaves infos unwritten. */
 #define GSVD_NOALLOC_MAX_PROBLEMS 4096
 int gsvd_solve_small_noalloc(const gsvd_problem *ps, int32_t count, const gsvd_config *cfg,
                              void *cuda_stream, gsvd_info *infos);

@@ -220,14 +220,27 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? GSVD_OK : (e == cudaE
     if (e_ != cudaSuccess) return cuda_status(e_); \
   } while (0)
 
-bool is_device_ptr(const void* p) {
+// Where a caller pointer lives: 1 = device memory of the current device (or
+// managed memory), 0 = host memory, -1 = device memory of another device.
+// The kernels run on the current device, so -1 is refused by every entry
+// point (a peer pointer would fault on the GPU instead of returning a status).
+int ptr_loc(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return 0;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return 1;
+  if (a.type != cudaMemoryTypeDevice) return 0;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return a.device == dev ? 1 : -1;
 }
+
+bool is_device_ptr(const void* p) { return ptr_loc(p) == 1; }
 
 // the shapes the library takes: 1 <= n <= 32768, n <= m_F, m_G <= 2^30
 bool shape_ok(int32_t dtype, int64_t mf, int64_t mg, int64_t n) {
@@ -818,9 +831,9 @@ int solve_any(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info, De
     info->status = v;
     return v;
   }
-  const bool dev = is_device_ptr(p->F);
-  if (dev != is_device_ptr(p->G) || dev != is_device_ptr(p->Z) || dev != is_device_ptr(p->sigma) ||
-      (p->X && dev != is_device_ptr(p->X))) {
+  const int dev = ptr_loc(p->F);
+  if (dev < 0 || dev != ptr_loc(p->G) || dev != ptr_loc(p->Z) || dev != ptr_loc(p->sigma) ||
+      dev != ptr_loc(p->sigma_f) || dev != ptr_loc(p->sigma_g) || (p->X && dev != ptr_loc(p->X))) {
     info->status = GSVD_EINVAL;
     return GSVD_EINVAL;
   }
@@ -962,7 +975,8 @@ int gsvd_solve_batched(gsvd_handle h, const gsvd_problem* ps, int32_t count, gsv
   std::vector<int> pw, blk;
   for (int k = 0; k < count; ++k) {
     int v = validate(&ps[k]);
-    if (v == GSVD_OK && !(is_device_ptr(ps[k].F) && is_device_ptr(ps[k].G) && is_device_ptr(ps[k].Z)))
+    if (v == GSVD_OK && !(is_device_ptr(ps[k].F) && is_device_ptr(ps[k].G) && is_device_ptr(ps[k].Z) &&
+                          is_device_ptr(ps[k].sigma_f) && is_device_ptr(ps[k].sigma_g) && is_device_ptr(ps[k].sigma)))
       v = GSVD_EINVAL;
     if (v == GSVD_OK && ps[k].X) v = GSVD_EINVAL;  // right vectors: gsvd_solve and gsvd_submit only
     if (v != GSVD_OK) {
@@ -1091,7 +1105,9 @@ int gsvd_submit(gsvd_handle h, const gsvd_problem* p, uint64_t* ticket) {
   if (!h || !ticket) return GSVD_EINVAL;
   int v = validate(p);
   if (v != GSVD_OK) return v;
-  if (!(is_device_ptr(p->F) && is_device_ptr(p->G) && is_device_ptr(p->Z))) return GSVD_EINVAL;
+  if (!(is_device_ptr(p->F) && is_device_ptr(p->G) && is_device_ptr(p->Z) && is_device_ptr(p->sigma_f) &&
+        is_device_ptr(p->sigma_g) && is_device_ptr(p->sigma)))
+    return GSVD_EINVAL;
   Plan P;
   const gsvd_config pc = cfg_for(h, p);
   if (!make_plan(pc, p->dtype, p->m_f, p->m_g, p->n, P)) return GSVD_EINVAL;

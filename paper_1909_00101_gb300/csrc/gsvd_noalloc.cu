@@ -36,13 +36,16 @@ void* g_dev_scratch[kMaxDevices] = {};    // device address of the array, per de
 PwProblem g_host_desc[kNoAllocMaxProblems];
 PwStats g_host_stat[kNoAllocMaxProblems];
 
-bool on_device(const void* p) {
+// device memory of the device dev (the current one), or managed memory: the
+// kernel runs on dev, so a pointer into another GPU's memory is refused
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -59,18 +62,23 @@ extern "C" int gsvd_solve_small_noalloc(const gsvd_problem* ps, int32_t count, c
     gsvd_config_default(&c);
   if (c.max_sweeps < 1 || (c.criterion != 1 && c.criterion != 2) || c.variant < 0 || c.variant > 3)
     return GSVD_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GSVD_ECUDA;
   // every problem must be a valid device problem that fits the pointwise kernel
+  // (the shape limits of gsvd_solve come first, so that no row count is
+  // narrowed to int before it is known to fit)
   const bool rowcyc = c.order == GSVD_ORDER_ROW_CYCLIC;
+  const int64_t kMaxRows = (int64_t)1 << 30;
   int slots = 1;
   for (int k = 0; k < count; ++k) {
     const gsvd_problem& p = ps[k];
     if ((p.dtype != GSVD_R64 && p.dtype != GSVD_C128) || p.n < 1 || p.m_f < p.n || p.m_g < p.n ||
-        p.ldf < p.m_f || p.ldg < p.m_g || p.ldz < p.n || !p.F || !p.G || !p.Z || !p.sigma_f || !p.sigma_g ||
-        !p.sigma || p.X)
+        p.m_f > kMaxRows || p.m_g > kMaxRows || p.ldf < p.m_f || p.ldg < p.m_g || p.ldz < p.n || !p.F || !p.G ||
+        !p.Z || !p.sigma_f || !p.sigma_g || !p.sigma || p.X)
       return GSVD_EINVAL;
     if (p.n > 64) return GSVD_ETOOBIG;
-    if (!on_device(p.F) || !on_device(p.G) || !on_device(p.Z) || !on_device(p.sigma_f) ||
-        !on_device(p.sigma_g) || !on_device(p.sigma))
+    if (!on_device(p.F, dev) || !on_device(p.G, dev) || !on_device(p.Z, dev) || !on_device(p.sigma_f, dev) ||
+        !on_device(p.sigma_g, dev) || !on_device(p.sigma, dev))
       return GSVD_EINVAL;
     const int n = (int)p.n;
     slots = std::max(slots, rowcyc ? std::max(1, n / 2) : std::max(1, (n + (n & 1)) / 2));
@@ -82,8 +90,6 @@ extern "C" int gsvd_solve_small_noalloc(const gsvd_problem* ps, int32_t count, c
   }
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   std::lock_guard<std::mutex> lk(g_mu);
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GSVD_ECUDA;
   // set-up, once per device (this device is current): the device address of
   // the array.  Host code must not pass &g_noalloc_scratch to a kernel: on the
   // host that name is a stand-in, not a device address.

@@ -1,5 +1,11 @@
-"""Multi-GPU stripe algorithm of Sec. 4: host-side schedule, exchange map and
-driver.
+"""A CPU simulation of the multi-GPU stripe algorithm of Sec. 4: the schedule,
+the exchange map and a host driver over processes.
+
+This is not the library's data plane.  Every call of this build gets one GPU,
+so the stripes, their exchange and the application of each pair's
+transformation to the pair's columns (a host matrix product) run on the host
+here, as CPU tensors between processes; the device work of a pair solve can
+be the library's (library_pair_solver) or, in the tests, the oracle's.
 
 The columns of F, G and Z are cut into ns = 2 s stripes of equal width (s
 processes, one per GPU).  In each outer step every process holds two stripes,
@@ -21,10 +27,10 @@ n not divisible into 2 s stripes of one width is bordered first (border,
 unborder: Sec. 3.1, Sec. 4.1).  solve() runs the whole method for a process
 that holds the full pair and gathers the GSVD on process 0.
 
-This module is host logic only (no arithmetic of the method): the pair solver
-is passed in.  On GPUs it is the library's own solve of the pair; the tests
-run it on CPU ranks.  Stripes travel as CPU tensors in a gloo group.  Any process that fails ends the others' waits by
-a timeout, which the driver reports as a status instead of hanging.
+The pair solver is passed in.  Stripes travel as CPU tensors in a gloo
+group.  Any process that fails ends the others' waits by a timeout, which
+the driver reports as a status instead of hanging; that holds for the final
+gather of solve() too.
 """
 from __future__ import annotations
 
@@ -295,6 +301,34 @@ def finalize(F: np.ndarray, G: np.ndarray, Z: np.ndarray) -> dict:
             "sigma_g": sg * th, "sigma": sf / sg}
 
 
+def _gather_parts(part, rank, world, dist, group, timeout_s):
+    """Process 0 collects every process's part (point to point: a length, then
+    the pickled bytes), each wait bounded by timeout_s.  Returns the list on
+    process 0 (None when a wait ran out: a peer failed), [] elsewhere (None
+    when its send timed out)."""
+    import pickle
+
+    import torch
+    tmo = timedelta(seconds=timeout_s)
+    try:
+        if rank != 0:
+            payload = torch.frombuffer(bytearray(pickle.dumps(part)), dtype=torch.uint8)
+            size = torch.tensor([payload.numel()], dtype=torch.int64)
+            dist.isend(size, dst=0, tag=101, group=group).wait(tmo)
+            dist.isend(payload, dst=0, tag=102, group=group).wait(tmo)
+            return []
+        parts = [part] + [None] * (world - 1)
+        for src in range(1, world):
+            size = torch.zeros(1, dtype=torch.int64)
+            dist.irecv(size, src=src, tag=101, group=group).wait(tmo)
+            payload = torch.empty(int(size.item()), dtype=torch.uint8)
+            dist.irecv(payload, src=src, tag=102, group=group).wait(tmo)
+            parts[src] = pickle.loads(payload.numpy().tobytes())
+        return parts
+    except RuntimeError:
+        return None
+
+
 def solve(F: np.ndarray, G: np.ndarray, *, rank: int, world: int, dist, solve_pair, unit: int = 1,
           max_sweeps: int = 30, timeout_s: float = 30.0, group=None):
     """The whole multi-process GSVD of Sec. 4 for one process that holds the
@@ -321,8 +355,9 @@ def solve(F: np.ndarray, G: np.ndarray, *, rank: int, world: int, dist, solve_pa
     if world == 1:
         parts = [part]
     else:
-        parts = [None] * world if rank == 0 else None
-        dist.gather_object(part, parts, dst=0, group=group)
+        parts = _gather_parts(part, rank, world, dist, group, timeout_s)
+        if parts is None:
+            return -6, None
     if rank != 0:
         return res.status, None
     status = 0

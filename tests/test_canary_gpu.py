@@ -3,9 +3,6 @@ larger allocation whose padding holds a canary value -- leading dimensions
 larger than the row counts (ld > m, odd paddings) and guard words after the
 sigma vectors.  After the solve the padding must be bitwise unchanged and the
 result must still be the oracle's GSVD (the solver honours ld everywhere).
-
-Written after the last GPU run of this tree; skipped until it has run on a
-GPU once.
 """
 import numpy as np
 import pytest
@@ -15,7 +12,7 @@ from paper_1909_00101_gb300.inputs import make_pair
 from gsvd_checks import rel_sigma_err
 
 torch = pytest.importorskip("torch")
-pytestmark = [pytest.mark.gpu, pytest.mark.skip(reason="not yet run on a GPU")]
+pytestmark = pytest.mark.gpu
 
 CANARY = -1234.5678
 

@@ -16,9 +16,15 @@ Integer outputs (status, convergence) must match exactly where defined.
 import numpy as np
 import pytest
 
+import os
+import sys
+
 import oracle
 from paper_1909_00101_gb300.inputs import make_pair, POINTWISE_64x32
 from gsvd_checks import invariants, rel_sigma_err
+
+sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+import oracle_cases  # noqa: E402
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -35,6 +41,17 @@ def hz():
     return m
 
 
+_big_pairs = {}
+
+
+def _big(recipe):
+    """A full-size pair, drawn once per test session (drawing it takes seconds)."""
+    key = tuple(sorted(recipe.items()))
+    if key not in _big_pairs:
+        _big_pairs[key] = make_pair(**recipe)
+    return _big_pairs[key]
+
+
 def _dev(a):
     return torch.from_numpy(np.asfortranarray(a)).cuda()
 
@@ -43,10 +60,35 @@ def _np(t):
     return t.cpu().numpy()
 
 
-def check(p_F, p_G, r, *, n_res=1e-13, label=""):
+def stored_or_live(p_F, p_G, case=None):
+    """(sigma_fp64, sigma_ext) of the oracle: the stored values of a case
+    (after the check that the pair is the stored one), else computed now."""
+    if case is not None:
+        rec = oracle_cases.load_checked(case, p_F, p_G)
+        assert rec["status_fp64"] == 0 and rec["status_ext"] == 0
+        return rec["sigma_fp64"], rec["sigma_ext"]
     ref = oracle.gsvd(p_F, p_G)
     refx = oracle.gsvd(p_F, p_G, extended=True)
     assert ref["status"] == 0 and refx["status"] == 0
+    return ref["sigma"], refx["sigma"]
+
+
+def sigma_vs_oracle(sig, p_F, p_G, case=None, label=""):
+    """The R14 rule: err(GPU vs oracle_ext) <= max(1e-12, 4 err(oracle_fp64
+    vs oracle_ext)); returns (err_ext, tol, err_fp64)."""
+    s64, sx = stored_or_live(p_F, p_G, case)
+    tol = max(1e-12, 4.0 * rel_sigma_err(s64, sx))
+    err_x = rel_sigma_err(sig, sx)
+    err_64 = rel_sigma_err(sig, s64)
+    print("%s sigma err vs oracle_ext %.2e (tol %.2e), vs oracle_fp64 %.2e" % (label, err_x, tol, err_64))
+    assert err_x <= tol, (label, err_x, tol)
+    return err_x, tol, err_64
+
+
+def check(p_F, p_G, r, *, n_res=1e-13, label="", case=None):
+    s64, sx = stored_or_live(p_F, p_G, case)
+    ref = {"sigma": s64}
+    refx = {"sigma": sx}
     sig = _np(r.sigma)
     floor = rel_sigma_err(ref["sigma"], refx["sigma"])
     tol = max(1e-12, 4.0 * floor)
@@ -307,6 +349,22 @@ def test_host_pointer_path_equals_device_path(hz):
     assert np.array_equal(_np(d.U), h.U)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batched_blocked_problems_vs_oracle(hz, precision):
+    """Problems of the 512-pair batch's distribution up to n = 256 (blocked
+    path, shortened where tall) in one batched call, each compared with the
+    oracle's sigma of that pair (stored) under the R14 rule; pointwise-size
+    problems in the same call against the oracle computed now."""
+    cases = ["batch_real_%d" % k for k in range(len(oracle_cases.BATCH_SHAPES))]
+    pairs = [make_pair(**oracle_cases.CASES[c]) for c in cases]
+    small = [make_pair(mf, mg, n, lo=1e-3, hi=1e3, cond=1e2, seed=1100 + k)
+             for k, (mf, mg, n) in enumerate([(40, 35, 30), (64, 48, 32), (20, 20, 16)])]
+    with hz.Solver(precision=precision) as s:
+        res = s.solve_batched([(_dev(p.F), _dev(p.G)) for p in pairs + small])
+    for c, p, r in zip(cases + [None] * len(small), pairs + small, res):
+        check(p.F, p.G, r, label="batched %s n=%d" % (precision, p.F.shape[1]), case=c)
+
+
 def test_batched_equals_single(hz):
     shapes = [(40, 35, 30), (64, 48, 32), (20, 20, 16), (90, 80, 70), (33, 33, 33)]
     pairs = [make_pair(*s, seed=100 + k) for k, s in enumerate(shapes)]
@@ -340,6 +398,8 @@ def test_serving_results_equal_alone_and_in_mix(hz):
         for k, (t, res) in enumerate(tickets):
             assert done[k][0] == 0, done[k]
             assert torch.equal(res.sigma, alone[k].sigma) and torch.equal(res.Z, alone[k].Z)
+            res.info = done[k][1]
+            check(pairs[k].F, pairs[k].G, res, label="served %s%s" % (shapes[k], " complex" if k % 3 == 2 else ""))
 
 
 # ---------------------------------------------------------------- status ----
@@ -386,10 +446,12 @@ def test_n_equal_one(hz):
 
 # ------------------------------------------------------------- full size ----
 
-def _full_size_checks(hz, p, r, n_sample=16):
-    """Properties that hold at any size, checked on the GPU in FP64, and the
-    generated sigma within n * eps * cond(X) (input rounding moves the exact
-    GSVD of the rounded pair by about eps * cond(X) per column)."""
+def _full_size_checks(hz, p, r, n_sample=16, case=None):
+    """Properties that hold at any size, checked on the GPU in FP64; the
+    oracle's sigma of this very pair (stored, keyed by the pair's SHA-256)
+    under the R14 rule; and the generated sigma within n * eps * cond(X)
+    (input rounding moves the exact GSVD of the rounded pair by about
+    eps * cond(X) per column)."""
     F0 = _dev(p.F)
     G0 = _dev(p.G)
     n = p.F.shape[1]
@@ -411,6 +473,8 @@ def _full_size_checks(hz, p, r, n_sample=16):
     assert scale <= 8 * eps
     assert np.all(np.diff(s_np) <= 0)
     assert rel <= n * eps * p.cond_x
+    if case is not None:
+        sigma_vs_oracle(s_np, p.F, p.G, case, label=case)
     # per-column backward errors of the GSVD relations on sampled columns:
     # ||F z_j - sigma_F,j u_j|| / (||F|| ||z_j||) and likewise for G (a check
     # through the Grams F*F, G*G would square the conditioning, App. G)
@@ -425,10 +489,10 @@ def _full_size_checks(hz, p, r, n_sample=16):
 def test_full_size_real_4096x2048_mixed(hz):
     """The benchmark workload in the benchmark's configuration (w = 16, BO, mixed)."""
     from paper_1909_00101_gb300.inputs import BLOCKED_REAL_4096x2048
-    p = make_pair(**BLOCKED_REAL_4096x2048)
+    p = _big(BLOCKED_REAL_4096x2048)
     r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", precision="mixed", inner_max_sweeps=1, max_sweeps=60,
                  fp32_max_sweeps=60)
-    _full_size_checks(hz, p, r)
+    _full_size_checks(hz, p, r, case="blocked_real_4096x2048")
     assert r.info["shortened"] == 1, r.info
     # the FP32 bulk sweeps converge on their own (FP32 Gram/apply are right)
     # and leave few FP64 sweeps
@@ -438,19 +502,58 @@ def test_full_size_real_4096x2048_mixed(hz):
 def test_full_size_real_4096x2048_unshortened(hz):
     """The same workload without the QR shortening (every sweep on 4096 rows)."""
     from paper_1909_00101_gb300.inputs import BLOCKED_REAL_4096x2048
-    p = make_pair(**BLOCKED_REAL_4096x2048)
+    p = _big(BLOCKED_REAL_4096x2048)
     r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", precision="mixed", inner_max_sweeps=1, max_sweeps=60,
                  fp32_max_sweeps=60, shorten=0)
-    _full_size_checks(hz, p, r)
+    _full_size_checks(hz, p, r, case="blocked_real_4096x2048")
     assert r.info["shortened"] == 0, r.info
 
 
 def test_full_size_complex_3072x1024_mixed(hz):
     from paper_1909_00101_gb300.inputs import BLOCKED_CPLX_3072x1024
-    p = make_pair(**BLOCKED_CPLX_3072x1024)
+    p = _big(BLOCKED_CPLX_3072x1024)
     r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", precision="mixed", block_w=8, inner_max_sweeps=1,
                  max_sweeps=80, fp32_max_sweeps=80)
-    _full_size_checks(hz, p, r)
+    _full_size_checks(hz, p, r, case="blocked_cplx_3072x1024")
+
+
+def test_full_size_real_4096x2048_fp64(hz):
+    """The benchmark workload in plain FP64 (the other arm of the benchmark)."""
+    from paper_1909_00101_gb300.inputs import BLOCKED_REAL_4096x2048
+    p = _big(BLOCKED_REAL_4096x2048)
+    r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", precision="fp64", inner_max_sweeps=1, max_sweeps=60)
+    _full_size_checks(hz, p, r, case="blocked_real_4096x2048")
+
+
+def test_full_size_complex_3072x1024_fp64(hz):
+    from paper_1909_00101_gb300.inputs import BLOCKED_CPLX_3072x1024
+    p = _big(BLOCKED_CPLX_3072x1024)
+    r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", precision="fp64", block_w=8, inner_max_sweeps=1,
+                 max_sweeps=80)
+    _full_size_checks(hz, p, r, case="blocked_cplx_3072x1024")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_mid_size_real_unshortened_vs_oracle(hz, precision):
+    """3000 + 2500 rows, n = 512, no shortening: every sweep runs on the full
+    rows, so the Gram takes several row splits per pair and the apply
+    hundreds of row tiles per launch; compared with the oracle's sigma of
+    this very pair (stored) under the R14 rule, with every invariant."""
+    case = "mid_real_3000x2500x512"
+    p = make_pair(**oracle_cases.CASES[case])
+    r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", block_w=16, precision=precision, shorten=0,
+                 inner_max_sweeps=1, max_sweeps=60, fp32_max_sweeps=60)
+    assert r.info["shortened"] == 0, r.info
+    check(p.F, p.G, r, label="mid-size real %s" % precision, case=case)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_mid_size_complex_vs_oracle(hz, precision):
+    case = "mid_cplx_1500x1200x256"
+    p = make_pair(**oracle_cases.CASES[case])
+    r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", block_w=8, precision=precision, inner_max_sweeps=1,
+                 max_sweeps=60, fp32_max_sweeps=60)
+    check(p.F, p.G, r, label="mid-size complex %s" % precision, case=case)
 
 
 def test_shortened_products_longer_than_one_exact_sum(hz):

@@ -262,3 +262,41 @@ def test_a_failed_rank_ends_the_others_waits(tmp_path):
     assert codes[1] != 0 and codes[0] == 0
     d = np.load(tmp_path / "r0.npz")
     assert int(d["status"]) == -6
+
+
+def _solve_fail_main(rank, world, port, out, F, G, fail_at):
+    import time
+    import torch.distributed as dist
+    from datetime import timedelta
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank, world_size=world,
+                            timeout=timedelta(seconds=60))
+    if rank == 1 and fail_at == "start":
+        raise SystemExit(3)                      # fails before its first step
+    if rank == 1 and fail_at == "gather":
+        def die(*a, **k):
+            raise SystemExit(3)                  # finishes its sweeps, fails before the gather
+        S._gather_parts = die
+    t0 = time.time()
+    st, res = S.solve(F, G, rank=rank, world=world, dist=dist, solve_pair=_solve_pair, timeout_s=3.0)
+    np.savez(os.path.join(out, "r%d.npz" % rank), status=st, seconds=time.time() - t0, has=res is not None)
+
+
+@pytest.mark.parametrize("fail_at", ["start", "gather"])
+def test_whole_solve_with_a_failed_rank_returns_a_status(tmp_path, fail_at):
+    """solve() on process 0 returns (-6, None) within its bounded waits when a
+    peer dies, before its first step or just before the final gather; it
+    never blocks for the process group's own (longer) timeout."""
+    from paper_1909_00101_gb300.inputs import make_pair
+    p = make_pair(40, 36, 16, seed=6)
+    ctx = pymp.get_context("spawn")
+    port = _port()
+    ps = [ctx.Process(target=_solve_fail_main, args=(r, 2, port, str(tmp_path), p.F, p.G, fail_at))
+          for r in range(2)]
+    for q in ps:
+        q.start()
+    for q in ps:
+        q.join(120)
+    assert ps[1].exitcode != 0 and ps[0].exitcode == 0
+    d = np.load(tmp_path / "r0.npz")
+    assert int(d["status"]) == -6 and not bool(d["has"])
+    assert float(d["seconds"]) < 40.0

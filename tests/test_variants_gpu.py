@@ -4,9 +4,6 @@ rescaling (+2), and with criterion C2 the variants 4-7.  Each case runs the
 library through the C ABI and the oracle in the same variant, with the
 tolerance of the other parity tests (extended-precision oracle, R14 rule) and
 the invariants; the row-cyclic order follows the oracle's sequence.
-
-The kernel variants were written after the last GPU run of this tree; the
-tests are skipped until they have run on a GPU once.
 """
 import numpy as np
 import pytest
@@ -16,7 +13,7 @@ from paper_1909_00101_gb300.inputs import make_pair, POINTWISE_64x32
 from gsvd_checks import invariants, rel_sigma_err
 
 torch = pytest.importorskip("torch")
-pytestmark = [pytest.mark.gpu, pytest.mark.skip(reason="kernel variants not yet run on a GPU")]
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
