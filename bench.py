@@ -415,62 +415,112 @@ def batched(args, hz, out):
                                      % (cores, dt, sum(x == 0 for x in st))}
 
 
+def _oracle_check(job):
+    """One oracle solve (process-pool worker): (index, err vs ext oracle, R14 tolerance)."""
+    k, F, G, sig = job
+    import oracle
+    r = oracle.gsvd(F, G)
+    rx = oracle.gsvd(F, G, extended=True)
+    if r["status"] != 0 or rx["status"] != 0:
+        return k, None, None
+    floor = float(np.max(np.abs(r["sigma"] - rx["sigma"]) / rx["sigma"]))
+    return k, float(np.max(np.abs(sig - rx["sigma"]) / rx["sigma"])), max(1e-12, 4.0 * floor)
+
+
 def serving(args, hz, out):
+    """c5: one seeded Poisson arrival trace served through gsvd_submit /
+    gsvd_poll by both arms (mixed and plain FP64) at the same rates, taken as
+    fractions of the plain-FP64 saturated throughput; p50/p99 latency from
+    arrival to the poll that sees the result; sigma of a stratified sample of
+    requests against the oracle (spawned host workers)."""
+    import multiprocessing as mp
     import torch
-    from paper_1909_00101_gb300.inputs import make_pair
-    rng = np.random.default_rng(0)
-    R = args.requests
+    from paper_1909_00101_gb300.inputs import make_pair, uniform
+    R, NP = args.requests, args.pool
+    # the pool of distinct pairs: n log-uniform in [32, 1024], m_F, m_G uniform
+    # in [n, 2n], real:complex 3:1, sigma in [1e-4, 1e4], cond(X) = 1e3
+    u = uniform(7, 0, 3 * NP)
     pool = []
-    for k in range(min(R, 40)):
-        n = int(round(np.exp(rng.uniform(np.log(32), np.log(1024)))))
-        mf, mg = int(rng.integers(n, 2 * n + 1)), int(rng.integers(n, 2 * n + 1))
-        cplx = (k % 4 == 3)
-        pool.append(make_pair(mf, mg, n, lo=1e-4, hi=1e4, cond=1e3, cplx=cplx, seed=2000 + k))
+    for k in range(NP):
+        n = int(round(np.exp(np.log(32) + (np.log(1024) - np.log(32)) * u[3 * k])))
+        mf = n + min(int(u[3 * k + 1] * (n + 1)), n)
+        mg = n + min(int(u[3 * k + 2] * (n + 1)), n)
+        pool.append(make_pair(mf, mg, n, lo=1e-4, hi=1e4, cond=1e3, cplx=(k % 4 == 3), seed=2000 + k))
     dev = [(_dev(q.F), _dev(q.G)) for q in pool]
-    order = [k % len(pool) for k in range(R)]
-    arms = {}
-    for prec in ("mixed", "fp64"):
-        with hz.Solver(precision=prec, inner_max_sweeps=1, max_sweeps=80, fp32_max_sweeps=80, max_inflight=16,
-                       hbm_budget_bytes=60 << 30, **lib_kw(args)) as s:
-            def run(arrivals):
+    rng = np.random.default_rng(11)
+    order = rng.integers(0, NP, R)
+    unit_gaps = rng.exponential(1.0, R)        # one trace, scaled to each rate
+    sat_n = min(R, args.sat_requests)
+
+    def run(s, arrivals, keep=None):
+        t0 = time.perf_counter()
+        pending, lat, ok, results = {}, [], 0, {}
+        k = 0
+        while k < len(arrivals) or pending:
+            now = time.perf_counter() - t0
+            while k < len(arrivals) and arrivals[k] <= now:
+                F, G = dev[order[k]]
+                t, res = s.submit(F, G)
+                pending[t] = (k, arrivals[k], res)
+                k += 1
+            for t in list(pending):
+                st, info = s.poll(t)
+                if st != hz.EAGAIN:
+                    kk, a, res = pending.pop(t)
+                    lat.append(time.perf_counter() - t0 - a)
+                    ok += st == 0
+                    if keep is not None and kk in keep:
+                        results[kk] = res.sigma.cpu().numpy()
+            time.sleep(0.0002)
+        return time.perf_counter() - t0, lat, ok, results
+
+    solvers = {prec: hz.Solver(precision=prec, inner_max_sweeps=1, max_sweeps=80, fp32_max_sweeps=80,
+                               max_inflight=16, hbm_budget_bytes=60 << 30, **lib_kw(args))
+               for prec in ("mixed", "fp64")}
+    arms = {prec: {} for prec in solvers}
+    # saturated throughput (the first sat_n requests of the trace, all at t = 0)
+    for prec, s in solvers.items():
+        run(s, [0.0] * min(32, sat_n))  # warm-up: the pool reserves its memory
+        T, lat, ok, _ = run(s, [0.0] * sat_n)
+        arms[prec]["saturated"] = {"requests": sat_n, "solves_per_s": sat_n / T, "ok": ok}
+    base = arms["fp64"]["saturated"]["solves_per_s"]
+    # stratified sample for the oracle: requests by n bin, small enough for the host
+    bins = [(32, 64), (64, 128), (128, 192)]
+    per_bin = max(1, args.oracle_sample // len(bins))
+    keep = set()
+    for lo_n, hi_n in bins:
+        idx = [k for k in range(R) if lo_n <= pool[order[k]].F.shape[1] < hi_n]
+        keep.update(idx[:per_bin])
+    for frac in args.loads:
+        lam = frac * base
+        arrivals = list(np.cumsum(unit_gaps / lam) - unit_gaps[0] / lam)
+        for prec, s in solvers.items():
+            T, lat, ok, res = run(s, arrivals, keep=keep)
+            ent = {"lambda_per_s": lam, "solves_per_s": R / T, "ok": ok,
+                   "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
+                   "latency_ms_p99": 1e3 * float(np.percentile(lat, 99))}
+            if prec == "mixed" and frac == args.loads[0] and keep:
+                ctx = mp.get_context("spawn")
+                cores = len(os.sched_getaffinity(0))
+                jobs = [(k, pool[order[k]].F, pool[order[k]].G, res[k]) for k in sorted(keep) if k in res]
                 t0 = time.perf_counter()
-                pending, lat, ok, results = {}, [], 0, {}
-                k = 0
-                while k < len(arrivals) or pending:
-                    now = time.perf_counter() - t0
-                    while k < len(arrivals) and arrivals[k] <= now:
-                        F, G = dev[order[k]]
-                        t, res = s.submit(F, G)
-                        pending[t] = (k, arrivals[k], res)
-                        k += 1
-                    for t in list(pending):
-                        st, info = s.poll(t)
-                        if st != hz.EAGAIN:
-                            kk, a, res = pending.pop(t)
-                            lat.append(time.perf_counter() - t0 - a)
-                            ok += st == 0
-                            results[kk] = res
-                    time.sleep(0.0005)
-                return time.perf_counter() - t0, lat, ok, results
-            # saturation: all requests at t = 0
-            T, lat, ok, results = run([0.0] * R)
-            thr = R / T
-            errs = [_err(results[k].sigma.cpu().numpy(), pool[order[k]].sigma) for k in range(R)]
-            # Poisson arrivals at 0.7 x the saturated throughput
-            lam = 0.7 * thr
-            gaps = np.random.default_rng(1).exponential(1.0 / lam, R)
-            T2, lat2, ok2, _ = run(list(np.cumsum(gaps) - gaps[0]))
-            arms[prec] = {"saturated_solves_per_s": thr, "ok": ok,
-                          "poisson_lambda_per_s": lam, "poisson_solves_per_s": R / T2, "poisson_ok": ok2,
-                          "latency_ms_p50": 1e3 * float(np.percentile(lat2, 50)),
-                          "latency_ms_p99": 1e3 * float(np.percentile(lat2, 99)),
-                          "max_rel_sigma_err_vs_construction": float(np.max(errs))}
+                with ctx.Pool(cores) as pp:
+                    chk = pp.map(_oracle_check, jobs, chunksize=1)
+                good = [c for c in chk if c[1] is not None]
+                out["oracle_check"] = {"requests": len(jobs), "cores": cores, "seconds": time.perf_counter() - t0,
+                                       "bins_n": bins, "max_err_vs_oracle_ext": max(c[1] for c in good),
+                                       "all_within_tolerance": all(c[1] <= c[2] for c in good)}
+            arms[prec]["load_%.2f" % frac] = ent
+    for s in solvers.values():
+        s.close()
     out["arms"] = arms
-    out["value"] = arms["mixed"]["poisson_solves_per_s"]
+    first = "load_%.2f" % args.loads[0]
+    out["value"] = arms["mixed"][first]["solves_per_s"]
     out["unit"] = "solves/s"
     out["metric"] = "GSVD serving: solves/s and p50/p99 latency, Poisson arrivals, mixed vs plain FP64"
-    out["config_extra"] = {"requests": R, "distinct_pairs": len(pool), "n_range": [32, 1024], "real_to_complex": "3:1",
-                           "hbm_budget_gib": 60, "max_inflight": 16}
+    out["config_extra"] = {"requests": R, "distinct_pairs": NP, "n_range": [32, 1024], "real_to_complex": "3:1",
+                           "hbm_budget_gib": 60, "max_inflight": 16, "loads_of_fp64_saturated": list(args.loads),
+                           "saturation_requests": sat_n, "trace_seed": 11}
 
 
 def run_mode(args):
@@ -511,7 +561,12 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "pointwise_real_F64x32_G48x32", "blocked_cplx_F3072x1024_G2048x1024",
                              "batched_real_512", "serving_poisson"])
-    ap.add_argument("--requests", type=int, default=160, help="serving: requests in the Poisson stream")
+    ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the Poisson stream")
+    ap.add_argument("--pool", type=int, default=200, help="serving: distinct pairs the requests draw from")
+    ap.add_argument("--sat-requests", type=int, default=400, help="serving: requests of the saturation runs")
+    ap.add_argument("--loads", type=float, nargs="+", default=[0.7, 0.9],
+                    help="serving: arrival rates as fractions of the plain-FP64 saturated throughput")
+    ap.add_argument("--oracle-sample", type=int, default=102, help="serving: requests checked by the oracle")
     args = ap.parse_args()
     if args.workload != WORKLOAD and args.impl == "ours":
         run_mode(args)

@@ -50,7 +50,7 @@ enum {
   GSVD_ENOCONV = -3,   /* sweep cap reached; outputs written */
   GSVD_ENOTPD = -4,    /* non-positive Cholesky pivot or 1 - x^2 <= 0 (rank-deficient G) */
   GSVD_EOVERFLOW = -5, /* non-finite column norm */
-  GSVD_ETIMEOUT = -6,  /* a bounded wait ran out */
+  GSVD_ETIMEOUT = -6,  /* the deadline timeout_ms passed; outputs finalised from the last sweep */
   GSVD_ECUDA = -7,     /* a CUDA runtime call failed */
   GSVD_ETOOBIG = -8    /* one request exceeds the memory budget */
 };
@@ -74,8 +74,17 @@ typedef struct {
   int32_t path;             /* GSVD_PATH_*: pointwise in-shared-memory or blocked */
   int32_t order;            /* pointwise pivot order: GSVD_ORDER_* */
   int32_t fp32_max_sweeps;  /* mixed precision: cap of the FP32 bulk sweeps (default 30) */
-  int32_t timeout_ms;       /* bound of host waits (0 = none) */
-  uint64_t hbm_budget_bytes;/* serving: device memory admitted at once (default 60 GiB) */
+  int32_t timeout_ms;       /* deadline of one blocked solve, counted from its start (the call for
+                               gsvd_solve, the start on a worker for gsvd_submit); 0 = none (default).
+                               Checked after every outer sweep: once it has passed no further sweep
+                               is issued, the outputs are finalised from that sweep's state (a valid
+                               decomposition, as after the sweep cap) and the status is
+                               GSVD_ETIMEOUT.  A host wait therefore ends at most one sweep and the
+                               finalisation after the deadline; the device is idle for that solve
+                               when the call returns.  The pointwise kernel (one launch) ignores it */
+  uint64_t hbm_budget_bytes;/* serving: device memory admitted at once (default 60 GiB): the
+                               workspaces of the requests on the GPU, which come from the handle's
+                               stream-ordered pool and return to it when a request ends */
   int32_t max_inflight;     /* serving: requests on the GPU at once (default 16) */
   int32_t profile;          /* 1 = time every Gram / inner / apply launch with CUDA events on the
                                solve's stream (gsvd_info.t_kernel_us); 0 = off (default) */
@@ -122,11 +131,11 @@ typedef struct {
   double *sigma_g;          /* out: diag(Sigma_G) */
   double *sigma;            /* out: Sigma = Sigma_F / Sigma_G */
   void *X;                  /* optional out (NULL = not wanted): the right generalized singular vectors
-                               X = Z^-1 (n x n), real problems, gsvd_solve and gsvd_submit (Sec. 1: X may
-                               be computed from Z).  Computed from the identity X = Sigma_F U^T F +
-                               Sigma_G V^T G, which holds because [U Sigma_F; V Sigma_G] has orthonormal
+                               X = Z^-1 (n x n, the problem's dtype), gsvd_solve and gsvd_submit (Sec. 1:
+                               X may be computed from Z).  Computed from the identity X = Sigma_F U^* F +
+                               Sigma_G V^* G, which holds because [U Sigma_F; V Sigma_G] has orthonormal
                                columns; the library keeps copies of F and G for it ((m_f + m_g) n
-                               doubles of device memory during the solve).  The GEVD of (F^T F, G^T G)
+                               elements of device memory during the solve).  The GEVD of (F^* F, G^* G)
                                is Z with Lambda = Sigma^2 */
   int64_t ldx;
 } gsvd_problem;
@@ -165,7 +174,12 @@ void gsvd_config_default(gsvd_config *cfg);
  * NULL = the legacy default stream.  One handle per host thread/stream. */
 int gsvd_create(gsvd_handle *h, const gsvd_config *cfg, void *cuda_stream);
 
-/* Destroy a handle: waits for its serving thread and frees its workspace. */
+/* Destroy a handle: waits for its serving threads and frees its workspace
+ * pool.  Workspaces of a handle come from a stream-ordered device memory pool
+ * of the current device, created at the handle's first solve; memory freed
+ * into it stays reserved for later workspaces until the handle is destroyed,
+ * so repeated solves allocate nothing new and never synchronize the device
+ * for an allocation. */
 int gsvd_destroy(gsvd_handle h);
 
 /* Solve one problem; blocks until the outputs are written.  info may be NULL.

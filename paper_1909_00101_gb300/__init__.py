@@ -113,7 +113,7 @@ def strerror(status: int) -> str:
 def make_config(precision="fp64", block_w=0, max_sweeps=30, inner_max_sweeps=30, criterion=1, sort=True,
                 path="auto", order="round_robin", fp32_max_sweeps=30, hbm_budget_bytes=60 << 30,
                 max_inflight=16, profile=False, inner_max_sweeps_fp32=1, shorten=1,
-                fp32_params=1, fp64_gemm=1, fp32_stop_permille=50, variant=0) -> Config:
+                fp32_params=1, fp64_gemm=1, fp32_stop_permille=50, variant=0, timeout_ms=0) -> Config:
     c = Config()
     load_library().gsvd_config_default(ctypes.byref(c))
     c.precision = PREC[precision]
@@ -134,6 +134,7 @@ def make_config(precision="fp64", block_w=0, max_sweeps=30, inner_max_sweeps=30,
     c.fp64_gemm = fp64_gemm
     c.fp32_stop_permille = fp32_stop_permille
     c.variant = variant
+    c.timeout_ms = timeout_ms
     return c
 
 
@@ -257,7 +258,7 @@ class Solver:
 
     def solve(self, F, G, *, inplace: bool = False, right_vectors: bool = False) -> Result:
         """GSVD of (F, G): torch CUDA tensors (device path) or numpy arrays (host
-        path).  right_vectors: also X = Z^-1 (real problems)."""
+        path).  right_vectors: also X = Z^-1."""
         dev, Fc, Gc, Z, sf, sg, sig = _prepare(F, G, inplace)
         p = _problem(Fc, Gc, Z, sf, sg, sig, dev)
         X = None

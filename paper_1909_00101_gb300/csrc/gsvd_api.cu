@@ -88,21 +88,67 @@ std::vector<uint16_t> row_cyclic_table(int n, int* steps, int* slots) {
   return t;
 }
 
+// Per-thread state of the call being served: the handle's stream-ordered
+// memory pool (workspaces come from it with cudaMallocFromPoolAsync and go
+// back with cudaFreeAsync, so no allocation or free synchronizes the device
+// once the pool holds the memory) and the solve's deadline (timeout_ms).
+struct CallState {
+  cudaMemPool_t pool = nullptr;
+  bool has_deadline = false;
+  std::chrono::steady_clock::time_point deadline;
+};
+thread_local CallState tl_call;
+
+struct CallScope {
+  CallState saved;
+  CallScope(cudaMemPool_t pool, int timeout_ms) : saved(tl_call) {
+    tl_call.pool = pool;
+    tl_call.has_deadline = timeout_ms > 0;
+    if (timeout_ms > 0)
+      tl_call.deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+  }
+  ~CallScope() { tl_call = saved; }
+  CallScope(const CallScope&) = delete;
+  CallScope& operator=(const CallScope&) = delete;
+};
+
+bool deadline_passed() {
+  return tl_call.has_deadline && std::chrono::steady_clock::now() >= tl_call.deadline;
+}
+
+// Device buffer from the calling thread's pool (stream-ordered on the stream
+// of its allocation), or cudaMalloc'ed when no pool is set.
 struct DevBuf {
   void* p = nullptr;
   size_t n = 0;
-  ~DevBuf() {
-    if (p) cudaFree(p);
-  }
-  cudaError_t ensure(size_t bytes) {
-    if (bytes <= n) return cudaSuccess;
-    if (p) cudaFree(p);
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t s = nullptr;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) {
+      if (pool)
+        cudaFreeAsync(p, s);
+      else
+        cudaFree(p);
+    }
     p = nullptr;
     n = 0;
-    cudaError_t e = cudaMalloc(&p, bytes);
-    if (e == cudaSuccess) n = bytes;
+  }
+  cudaError_t ensure(size_t bytes, cudaStream_t st) {
+    if (bytes <= n && st == s) return cudaSuccess;
+    release();
+    pool = tl_call.pool;
+    s = st;
+    cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, st) : cudaMalloc(&p, bytes);
+    if (e == cudaSuccess)
+      n = bytes;
+    else
+      p = nullptr;
     return e;
   }
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
 };
 
 struct Plan {
@@ -254,7 +300,7 @@ int validate(const gsvd_problem* p) {
   if (!shape_ok(p->dtype, p->m_f, p->m_g, p->n)) return GSVD_EINVAL;
   if (p->ldf < p->m_f || p->ldg < p->m_g || p->ldz < p->n) return GSVD_EINVAL;
   if (!p->F || !p->G || !p->Z || !p->sigma_f || !p->sigma_g || !p->sigma) return GSVD_EINVAL;
-  if (p->X && (p->dtype != GSVD_R64 || p->ldx < p->n)) return GSVD_EINVAL;
+  if (p->X && p->ldx < p->n) return GSVD_EINVAL;
   return GSVD_OK;
 }
 
@@ -271,6 +317,7 @@ struct Request {
 struct gsvd_ctx {
   gsvd_config cfg;
   cudaStream_t stream;
+  cudaMemPool_t pool = nullptr;         // stream-ordered workspace pool of the handle
   DevBuf ws;
   unsigned long long* h_ctr = nullptr;  // pinned counters (NCTR)
   // serving
@@ -444,6 +491,12 @@ int run_sweeps(const Plan& P, const gsvd_config& cfg, bool fp32, void* F, long l
       converged = true;
       break;
     }
+    if (deadline_passed()) {
+      // timeout_ms: no further sweep is issued; the outputs are finalised
+      // from this sweep's state, as after the sweep cap
+      *sweeps_out = sw;
+      return GSVD_ETIMEOUT;
+    }
     // FP32 bulk sweeps hand over to the FP64 sweeps once few of their
     // transformations are big: the FP64 sweep count no longer falls after
     // that point, while every further FP32 sweep costs a full sweep
@@ -472,7 +525,7 @@ int solve_pointwise(const gsvd_config& cfg, const gsvd_problem* ps, const int* i
   }
   const size_t pb = align256(sizeof(PwProblem) * count);
   DevBuf tmp;
-  CK(tmp.ensure(2 * pb + sizeof(PwStats) * count));
+  CK(tmp.ensure(2 * pb + sizeof(PwStats) * count, s));
   unsigned char* base = static_cast<unsigned char*>(tmp.p);
   PwStats* d_stats = reinterpret_cast<PwStats*>(base + 2 * pb);
   CK(cudaMemsetAsync(d_stats, 0, sizeof(PwStats) * count, s));
@@ -562,7 +615,7 @@ int solve_plain(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info, 
                 unsigned long long* h_ctr, cudaStream_t s) {
   Plan P;
   if (!make_plan(cfg, p->dtype, p->m_f, p->m_g, p->n, P)) return GSVD_EINVAL;
-  CK(ws.ensure(P.total));
+  CK(ws.ensure(P.total, s));
   unsigned char* w = static_cast<unsigned char*>(ws.p);
   SolveEvents ev;
   cudaEvent_t e0 = ev.e0, e1 = ev.e1, e2 = ev.e2;
@@ -664,7 +717,7 @@ int solve_shortened(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* in
   double* G = (double*)p->G;
   const size_t nn = (size_t)n * n;
   const size_t tmp = (size_t)std::max(mf, mg) * n;
-  CK(ws.ensure(shortened_total(cfg, mf, mg, n)));
+  CK(ws.ensure(shortened_total(cfg, mf, mg, n), s));
   double* RF = reinterpret_cast<double*>(static_cast<unsigned char*>(ws.p) + shortened_offset(cfg, n));
   double* RG = RF + nn;
   double* R1F = RG + nn;
@@ -769,19 +822,27 @@ int solve_device(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info,
                  unsigned long long* h_ctr, cudaStream_t s) {
   if (!p->X) return solve_device_core(cfg, p, info, ws, h_ctr, s);
   const int n = (int)p->n, mf = (int)p->m_f, mg = (int)p->m_g;
+  const bool cplx = p->dtype == GSVD_C128;
+  const size_t E = cplx ? 2 : 1;
   DevBuf keep;
-  CK(keep.ensure(sizeof(double) * (((size_t)mf + mg) * n + (size_t)n * n) + 256));
+  CK(keep.ensure(sizeof(double) * E * (((size_t)mf + mg) * n + (size_t)n * n) + 256, s));
   double* F0 = static_cast<double*>(keep.p);
-  double* G0 = F0 + (size_t)mf * n;
-  double* T = G0 + (size_t)mg * n;
-  CK(cudaMemcpy2DAsync(F0, (size_t)mf * 8, p->F, p->ldf * 8, (size_t)mf * 8, n, cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemcpy2DAsync(G0, (size_t)mg * 8, p->G, p->ldg * 8, (size_t)mg * 8, n, cudaMemcpyDeviceToDevice, s));
+  double* G0 = F0 + E * mf * n;
+  double* T = G0 + E * mg * n;
+  CK(cudaMemcpy2DAsync(F0, E * mf * 8, p->F, p->ldf * 8 * E, E * mf * 8, n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpy2DAsync(G0, E * mg * 8, p->G, p->ldg * 8 * E, E * mg * 8, n, cudaMemcpyDeviceToDevice, s));
   const int st = solve_device_core(cfg, p, info, ws, h_ctr, s);
-  if (st != GSVD_OK && st != GSVD_ENOCONV) return st;
+  if (st != GSVD_OK && st != GSVD_ENOCONV && st != GSVD_ETIMEOUT) return st;
   double* X = static_cast<double*>(p->X);
-  CK(dgemm(true, false, n, n, mf, 1.0, (const double*)p->F, p->ldf, F0, mf, 0.0, X, p->ldx, 0, s));
-  CK(dgemm(true, false, n, n, mg, 1.0, (const double*)p->G, p->ldg, G0, mg, 0.0, T, n, 0, s));
-  CK(launch_rows_combine(n, X, p->ldx, p->sigma_f, T, n, p->sigma_g, s));
+  if (cplx) {
+    // X = Sigma_F U^H F + Sigma_G V^H G ([U Sigma_F; V Sigma_G] has orthonormal columns)
+    CK(launch_gemm_ch(mf, n, n, (const double*)p->F, p->ldf, F0, mf, X, p->ldx, s));
+    CK(launch_gemm_ch(mg, n, n, (const double*)p->G, p->ldg, G0, mg, T, n, s));
+  } else {
+    CK(dgemm(true, false, n, n, mf, 1.0, (const double*)p->F, p->ldf, F0, mf, 0.0, X, p->ldx, 0, s));
+    CK(dgemm(true, false, n, n, mg, 1.0, (const double*)p->G, p->ldg, G0, mg, 0.0, T, n, 0, s));
+  }
+  CK(launch_rows_combine(n, cplx, X, p->ldx, p->sigma_f, T, n, p->sigma_g, s));
   CK(cudaStreamSynchronize(s));
   return st;
 }
@@ -795,7 +856,7 @@ int solve_host(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info, D
                bZ = align256((size_t)p->n * p->n * es), bv = align256((size_t)p->n * 8);
   DevBuf stage;
   const size_t bX = p->X ? align256((size_t)p->n * p->n * es) : 0;
-  CK(stage.ensure(bF + bG + bZ + 3 * bv + bX));
+  CK(stage.ensure(bF + bG + bZ + 3 * bv + bX, s));
   unsigned char* b = static_cast<unsigned char*>(stage.p);
   gsvd_problem d = *p;
   d.F = b; d.ldf = p->m_f;
@@ -843,7 +904,6 @@ int solve_any(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info, De
 void worker_loop(gsvd_ctx* h) {
   cudaStream_t s;
   cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-  DevBuf ws;
   unsigned long long* h_ctr = nullptr;
   cudaMallocHost(&h_ctr, NCTR * sizeof(unsigned long long));
   for (;;) {
@@ -869,7 +929,18 @@ void worker_loop(gsvd_ctx* h) {
     }
     gsvd_info info;
     std::memset(&info, 0, sizeof info);
-    solve_device(cfg_for(h, &r->prob), &r->prob, &info, ws, h_ctr, s);
+    {
+      // the request's workspace comes from the handle's pool and goes back to
+      // it when the request ends (stream-ordered: no device-wide
+      // synchronisation), so the memory held by the handle stays within the
+      // budget that admission counts
+      CallScope call(h->pool, h->cfg.timeout_ms);
+      DevBuf ws;
+      const int st = solve_device(cfg_for(h, &r->prob), &r->prob, &info, ws, h_ctr, s);
+      if (st != GSVD_OK && info.status == GSVD_OK) info.status = st;
+      ws.release();
+      cudaStreamSynchronize(s);
+    }
     {
       std::lock_guard<std::mutex> lk(h->mu);
       r->info = info;
@@ -919,7 +990,7 @@ int gsvd_create(gsvd_handle* h, const gsvd_config* cfg, void* stream) {
     c->cfg = *cfg;
   else
     gsvd_config_default(&c->cfg);
-  if (c->cfg.max_sweeps < 1 || c->cfg.inner_max_sweeps < 1 || c->cfg.fp32_max_sweeps < 0 ||
+  if (c->cfg.max_sweeps < 1 || c->cfg.inner_max_sweeps < 1 || c->cfg.fp32_max_sweeps < 0 || c->cfg.timeout_ms < 0 ||
       (c->cfg.criterion != 1 && c->cfg.criterion != 2) || c->cfg.max_inflight < 1 ||
       c->cfg.variant < 0 || c->cfg.variant > 3 ||
       (c->cfg.precision != GSVD_PREC_FP64 && c->cfg.precision != GSVD_PREC_MIXED)) {
@@ -939,14 +1010,38 @@ int gsvd_destroy(gsvd_handle h) {
   }
   h->cv.notify_all();
   for (auto& t : h->workers) t.join();
+  h->ws.release();
+  if (h->pool) {
+    cudaStreamSynchronize(h->stream);
+    cudaMemPoolDestroy(h->pool);
+  }
   if (h->h_ctr) cudaFreeHost(h->h_ctr);
   delete h;
   return GSVD_OK;
 }
 
+// First use of a handle on its device: pinned counters and the workspace pool
+// (device memory of the current device; memory freed into it stays reserved
+// for the next workspace until the handle is destroyed).
 static int ensure_pinned(gsvd_handle h) {
-  if (h->h_ctr) return GSVD_OK;
-  return cudaMallocHost(&h->h_ctr, NCTR * sizeof(unsigned long long)) == cudaSuccess ? GSVD_OK : GSVD_ECUDA;
+  std::lock_guard<std::mutex> lk(h->mu);
+  if (!h->h_ctr && cudaMallocHost(&h->h_ctr, NCTR * sizeof(unsigned long long)) != cudaSuccess) return GSVD_ECUDA;
+  if (!h->pool) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GSVD_ECUDA;
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    if (cudaMemPoolCreate(&h->pool, &props) != cudaSuccess) {
+      h->pool = nullptr;
+      return GSVD_ECUDA;
+    }
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(h->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  return GSVD_OK;
 }
 
 int gsvd_solve(gsvd_handle h, const gsvd_problem* p, gsvd_info* info) {
@@ -960,7 +1055,9 @@ int gsvd_solve(gsvd_handle h, const gsvd_problem* p, gsvd_info* info) {
   }
   int pe = ensure_pinned(h);
   if (pe != GSVD_OK) return pe;
+  CallScope call(h->pool, h->cfg.timeout_ms);
   int st = solve_any(cfg_for(h, p), p, &tmp, h->ws, h->h_ctr, h->stream);
+  if (st != GSVD_OK && tmp.status == GSVD_OK) tmp.status = st;  // the report carries the returned status
   if (info) *info = tmp;
   return st;
 }
@@ -1001,12 +1098,19 @@ int gsvd_solve_batched(gsvd_handle h, const gsvd_problem* ps, int32_t count, gsv
     pool.emplace_back([&]() {
       cudaStream_t s;
       if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return;
-      DevBuf ws;
-      unsigned long long* hc = nullptr;
-      if (cudaMallocHost(&hc, NCTR * sizeof(unsigned long long)) == cudaSuccess) {
-        for (int q = next.fetch_add(1); q < (int)blk.size(); q = next.fetch_add(1))
-          solve_device(cfg_for(h, &ps[blk[q]]), &ps[blk[q]], &loc[blk[q]], ws, hc, s);
-        cudaFreeHost(hc);
+      {
+        CallScope call(h->pool, h->cfg.timeout_ms);
+        DevBuf ws;
+        unsigned long long* hc = nullptr;
+        if (cudaMallocHost(&hc, NCTR * sizeof(unsigned long long)) == cudaSuccess) {
+          for (int q = next.fetch_add(1); q < (int)blk.size(); q = next.fetch_add(1)) {
+            gsvd_info& in = loc[blk[q]];
+            const int st = solve_device(cfg_for(h, &ps[blk[q]]), &ps[blk[q]], &in, ws, hc, s);
+            if (st != GSVD_OK && in.status == GSVD_OK) in.status = st;
+          }
+          cudaFreeHost(hc);
+        }
+        ws.release();
       }
       cudaStreamSynchronize(s);
       cudaStreamDestroy(s);
@@ -1035,12 +1139,13 @@ int gsvd_autotune(gsvd_handle h, int32_t dtype, int64_t m_f, int64_t m_g, int64_
   if (P0.path != GSVD_PATH_BLOCKED || h->cfg.block_w != 0) return GSVD_OK;  // nothing to choose
   int pe = ensure_pinned(h);
   if (pe != GSVD_OK) return pe;
+  CallScope call(h->pool, 0);
   const bool cplx = dtype == GSVD_C128;
   const int E = cplx ? 2 : 1;
   // a synthetic pair of this shape (hash-based values in [-1, 1))
   DevBuf buf;
   const size_t nF = (size_t)m_f * n * E, nG = (size_t)m_g * n * E, nZ = (size_t)n * n * E;
-  CK(buf.ensure(sizeof(double) * (nF + nG + nZ + 3 * (size_t)n) + 256));
+  CK(buf.ensure(sizeof(double) * (nF + nG + nZ + 3 * (size_t)n) + 256, h->stream));
   double* F = static_cast<double*>(buf.p);
   double* G = F + nF;
   double* Z = G + nG;
@@ -1111,8 +1216,13 @@ int gsvd_submit(gsvd_handle h, const gsvd_problem* p, uint64_t* ticket) {
   Plan P;
   const gsvd_config pc = cfg_for(h, p);
   if (!make_plan(pc, p->dtype, p->m_f, p->m_g, p->n, P)) return GSVD_EINVAL;
-  const uint64_t bytes = solve_bytes(pc, P, p->m_f, p->m_g, p->n);
+  uint64_t bytes = solve_bytes(pc, P, p->m_f, p->m_g, p->n);
+  if (p->X)
+    bytes += sizeof(double) * (p->dtype == GSVD_C128 ? 2 : 1) *
+                 ((uint64_t)(p->m_f + p->m_g) * p->n + (uint64_t)p->n * p->n) + 256;
   if (bytes > h->cfg.hbm_budget_bytes) return GSVD_ETOOBIG;
+  int pe = ensure_pinned(h);
+  if (pe != GSVD_OK) return pe;
   std::unique_ptr<Request> r(new Request);
   r->prob = *p;
   std::memset(&r->info, 0, sizeof r->info);

@@ -82,6 +82,20 @@ __device__ __forceinline__ double p_abs(double x) { return fabs(x); }
 __device__ __forceinline__ float p_abs(float x) { return fabsf(x); }
 __device__ __forceinline__ double p_fma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float p_fma(float a, float b, float c) { return fmaf(a, b, c); }
+// below lim() the square of a value may lose bits to underflow; up() is a
+// power of two that brings such values back into the normal range
+template <class T>
+struct TinyScale;
+template <>
+struct TinyScale<double> {
+  static __device__ __forceinline__ double lim() { return 0x1p-900; }
+  static __device__ __forceinline__ double up() { return 0x1p+450; }
+};
+template <>
+struct TinyScale<float> {
+  static __device__ __forceinline__ float lim() { return 0x1p-100f; }
+  static __device__ __forceinline__ float up() { return 0x1p+50f; }
+};
 // "rounds to 1 in FP32" (the small-transformation class of the FP32 sweeps)
 __device__ __forceinline__ bool f32_is_one(double x) { return __double2float_rn(x) == 1.0f; }
 __device__ __forceinline__ bool f32_is_one(float x) { return x == 1.0f; }
@@ -118,11 +132,14 @@ enum : int { PV_ROT = 1, PV_BIG = 2, PV_SWAP = 4, PV_FAIL = 8 };
 //   chain B: xi = x / (sqrt(1+x) + sqrt(1-x)) and
 //            eta = x / ((1 + sqrt(1+x)) (1 + sqrt(1-x)));
 //   combine: cos/sin of phi and psi, Z-hat, sorting and the small/big class.
-// The chain below is the paper's, rearranged to need 7 instead of 11 square
-// roots and divisions: 1/t and t from one rsqrt; xi and eta from one
-// reciprocal; tan theta = sign(1, cot 2theta) / (|cot 2theta| +
-// sqrt(1 + cot^2 2theta)) written on num/den without forming the cotangent:
-// sign(num) den / (|num| + hypot(num, den)).
+// The chain below is the paper's, rearranged so that every square root and
+// division is a reciprocal square root (the shortest FP64 sequence): 1/t and
+// t from one rsqrt; with cot 2theta = num/den and r = 1/hypot(num, den),
+// cos 2theta = |num| r and sin 2theta = sign(num) den r (the angle with
+// |theta| <= pi/4 that sign(1, cot 2theta) / (|cot 2theta| + sqrt(1 +
+// cot^2 2theta)) selects), then cos^2 theta = (1 + cos 2theta) / 2 and
+// cos theta = q rsqrt(q), sin theta = sin 2theta rsqrt(q) / 2; sqrt(1 +- x)
+// = (1 +- x) rsqrt(1 +- x); xi and eta from one rsqrt squared.
 // T = double in the FP64 sweeps; T = float in the FP32 bulk sweeps, whose
 // inputs (dot products of FP32 columns) carry FP32 errors anyway.
 enum : int { RC_SKIP = 0, RC_ROT = 1, RC_EXC = 2, RC_FAIL = 3 };
@@ -166,19 +183,31 @@ __device__ __forceinline__ RealChainAT<T> real_chain_a(T a11, T a22, T a12, T x,
     r.mode = RC_EXC;  // proportional pivots: cot 2theta = 0/0
     return r;
   }
-  const T hyp = p_sqrt(p_fma(num, num, den * den));
-  const T tn = sgn1(num) * den / (p_abs(num) + hyp);
-  r.c = p_rsqrt(p_fma(tn, tn, T(1)));
-  r.s = tn * r.c;
+  T h2 = p_fma(num, num, den * den);
+  T nu = num, de = den;
+  if (h2 < TinyScale<T>::lim()) {  // squares near underflow: scale by a power of two first
+    nu = num * TinyScale<T>::up();
+    de = den * TinyScale<T>::up();
+    h2 = p_fma(nu, nu, de * de);
+  }
+  const T rh = p_rsqrt(h2);
+  const T c2 = p_abs(nu) * rh;            // cos 2theta >= 0
+  const T s2 = sgn1(num) * de * rh;       // sin 2theta
+  const T q = p_fma(T(0.5), c2, T(0.5));  // cos^2 theta in [1/2, 1]
+  const T rq = p_rsqrt(q);
+  r.c = q * rq;
+  r.s = T(0.5) * s2 * rq;
   r.mode = RC_ROT;
   return r;
 }
 
 template <class T>
 __device__ __forceinline__ void real_chain_b(T x, T& xi, T& eta) {
-  const T sp = p_sqrt(T(1) + x), sm = p_sqrt(T(1) - x);
+  const T up = T(1) + x, um = T(1) - x;
+  const T sp = up * p_rsqrt(up), sm = um * p_rsqrt(um);
   const T q1 = sp + sm, q2 = (T(1) + sp) * (T(1) + sm);
-  const T rq = T(1) / (q1 * q2);
+  const T rP = p_rsqrt(q1 * q2);
+  const T rq = rP * rP;  // 1 / (q1 q2)
   xi = x * q2 * rq;
   eta = x * q1 * rq;
 }

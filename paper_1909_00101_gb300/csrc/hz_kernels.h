@@ -127,8 +127,11 @@ cudaError_t launch_gemm_f64_by_f32(int m, int n, bool cplx, const double* A, lon
 cudaError_t launch_fill_hash(int rows, int n, unsigned seed, double* A, long long lda, cudaStream_t s);
 // X(i, j) <- sf_i X(i, j) + sg_i T(i, j) (n x n): the right vectors from
 // U^T F (in X) and V^T G (in T)
-cudaError_t launch_rows_combine(int n, double* X, long long ldx, const double* sf, const double* T, long long ldt,
-                                const double* sg, cudaStream_t s);
+cudaError_t launch_rows_combine(int n, bool cplx, double* X, long long ldx, const double* sf, const double* T,
+                                long long ldt, const double* sg, cudaStream_t s);
+// C = A^H B, complex interleaved (right vectors of complex problems)
+cudaError_t launch_gemm_ch(int m, int k, int n, const double* A, long long lda, const double* B, long long ldb,
+                           double* C, long long ldc, cudaStream_t s);
 // Z64 = diag(zdiag) * Z32 (rows scaled), FP64 result
 cudaError_t launch_rowscale(int n, bool cplx, const double* zdiag, const float* Z32, long long ld32,
                             double* Z, long long ldz, cudaStream_t s);

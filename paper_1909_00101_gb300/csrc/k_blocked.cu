@@ -17,7 +17,10 @@
 // pair leaves most SMs idle for n = 2048).  Complex data is handled by real
 // views: with W = [Re Y, Im Y], Re(Y^*Y) and Im(Y^*Y) are sums and differences
 // of blocks of W^T W, and Y Z = [Re Y, Im Y] [[Re Z, Im Z], [-Im Z, Re Z]].
+#include <cstdlib>
 #include <type_traits>
+
+#include <cooperative_groups.h>
 
 #include "blk_pair.cuh"
 #include "hz_device.cuh"
@@ -801,6 +804,472 @@ __global__ void __launch_bounds__(INNER_THREADS) k_inner(BlkDims d, BlkBuffers b
   }
 }
 
+// ------------------------------------------- inner, two-CTA cluster ----
+// The FP64 pivot step of one pair on a cluster of two CTAs, i.e. two SMs.
+// On sm_103a an SM issues about one FP64 warp instruction per 16 cycles, so
+// one CTA per pair leaves the dots and column updates of every inner step
+// throughput-bound on one SM while, with 64 pairs, 88 of the 152 SMs idle.
+// Here the rows of F-hat, G-hat and Z-hat are split between the two CTAs:
+//   * both CTAs sum the Gram partials and factor A-hat and B-hat (the same
+//     fixed-order arithmetic, so the same bits), then keep their own half of
+//     the rows of the Cholesky factors;
+//   * per inner step each CTA forms the dot products over its rows, two
+//     pairs per warp (one per 16-lane half), and the two halves of every
+//     dot product are added through distributed shared memory -- a + b is
+//     the same in both CTAs, so both compute the same 2x2 parameters and
+//     take the same decisions (sorting, counters, stopping) without further
+//     exchange;
+//   * each CTA applies the transformations to its own rows; Theta-tilde
+//     takes one more exchange of partial column norms.
+// One cluster barrier per inner step; the partial dot products are double
+// buffered so that a CTA never overwrites values its peer has yet to read.
+// Every exit after the first exchange passes one more cluster barrier, so no
+// CTA leaves while its peer may still read its shared memory.
+constexpr int INNER2_THREADS = 256;
+
+// Reduce-scatter of four per-lane values inside each 16-lane half of a warp
+// (2 + 1 + 1 + 1 = 5 adds, fixed order): value q = 2 (lane bit 3) + (lane
+// bit 2), summed over the half, is returned on its four lanes.
+__device__ __forceinline__ double half_sum4(const double v[4]) {
+  const int lane = threadIdx.x & 31;
+  const bool b8 = lane & 8;
+  const double s0 = b8 ? v[0] : v[2], s1 = b8 ? v[1] : v[3];
+  double k0 = b8 ? v[2] : v[0], k1 = b8 ? v[3] : v[1];
+  k0 += __shfl_xor_sync(FULL, s0, 8);
+  k1 += __shfl_xor_sync(FULL, s1, 8);
+  const bool b4 = lane & 4;
+  const double sx = b4 ? k0 : k1;
+  double k = b4 ? k1 : k0;
+  k += __shfl_xor_sync(FULL, sx, 4);
+  k += __shfl_xor_sync(FULL, k, 2);
+  k += __shfl_xor_sync(FULL, k, 1);
+  return k;
+}
+
+template <bool CPLX, int V>
+size_t inner2_smem() {
+  constexpr int E = CPLX ? 2 : 1;
+  constexpr int BMAX = CPLX ? V / 2 : V;
+  constexpr int RH = (BMAX + 1) / 2;
+  constexpr int NPMAX = BMAX / 2;
+  return sizeof(double) * (2 * E * BMAX * BMAX + 3 * E * RH * BMAX + 2 * NPMAX * 8 + 2 * BMAX) +
+         sizeof(PivInT<double>) * (NPMAX + 1) + sizeof(PivZ<double>) * (NPMAX + 1) +
+         sizeof(uint16_t) * (BMAX * (BMAX + 1) / 2) + 16;
+}
+
+template <bool CPLX, int V>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(INNER2_THREADS)
+    k_inner2(BlkDims d, BlkBuffers b, int step, InnerParams prm) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  constexpr int E = CPLX ? 2 : 1;
+  constexpr int BMAX = CPLX ? V / 2 : V;  // max columns of the pair
+  constexpr int RH = (BMAX + 1) / 2;      // max rows of a CTA
+  constexpr int NPMAX = BMAX / 2;         // max pairs of an inner step
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* A = reinterpret_cast<double*>(smem_raw);  // E BMAX x BMAX, column-major (ld BMAX)
+  double* Bm = A + E * BMAX * BMAX;
+  double* Fl = Bm + E * BMAX * BMAX;                // own rows: E RH x BMAX, column-major
+  double* Gl = Fl + E * RH * BMAX;
+  double* Zl = Gl + E * RH * BMAX;
+  double* part = Zl + E * RH * BMAX;                // [2][NPMAX][8] partial dot products
+  double* nrm = part + 2 * NPMAX * 8;               // [BMAX] partial column norms
+  double* th = nrm + BMAX;                          // [BMAX] prescale z_j, then theta_j
+  PivInT<double>* pin = reinterpret_cast<PivInT<double>*>(th + BMAX);
+  PivZ<double>* pout = reinterpret_cast<PivZ<double>*>(pin + NPMAX + 1);
+  uint16_t* s_tri = reinterpret_cast<uint16_t*>(pout + NPMAX + 1);
+  __shared__ int s_ctr[4];  // all, big, fail, any-change
+  __shared__ double s_inv[2];
+  __shared__ int s_bad;
+  __shared__ double s_xi[32], s_eta[32];
+  __shared__ unsigned char s_pair[63][32][2];
+
+  const int rank = (int)cluster.block_rank();
+  const int slot = blockIdx.x >> 1;
+  PairCols pc;
+  if (!load_pair(d, b, step, slot, pc)) return;  // the same answer in both CTAs
+  const int bb = pc.bb;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int S = d.rf + d.rg;
+  const double* P = static_cast<const double*>(b.partial) + (size_t)slot * S * V * V;
+  const bool lead = rank == 0 && threadIdx.x == 0;
+  if (threadIdx.x < 4) s_ctr[threadIdx.x] = 0;
+  if (threadIdx.x == 0) s_bad = 0;
+  if (lead) atomicAdd(&b.ctr[4], 1ull);
+  const int nup = bb * (bb + 1) / 2;
+  for (int u = threadIdx.x; u < nup; u += blockDim.x) {
+    int i, j;
+    unpack_upper(u, i, j);
+    s_tri[u] = (uint16_t)(i | (j << 8));
+  }
+  __syncthreads();
+
+  // 1. fixed-order sum of the partials into A-hat and B-hat (both triangles)
+  for (int t = threadIdx.x; t < 2 * nup; t += blockDim.x) {
+    const int mat = t >= nup ? 1 : 0;
+    const int ij = s_tri[nup - 1 - (t - mat * nup)];
+    const int i = bb - 1 - (ij >> 8), j = bb - 1 - (ij & 255);
+    const int s0 = mat ? d.rf : 0, s1 = mat ? S : d.rf;
+    double* M = mat ? Bm : A;
+    double re = 0.0, im = 0.0;
+#pragma unroll 8
+    for (int sp = s0; sp < s1; ++sp) {
+      const double* Q = P + (size_t)sp * V * V;
+      if constexpr (!CPLX) {
+        re += Q[i * V + j];
+      } else {
+        re += Q[i * V + j] + Q[(bb + i) * V + bb + j];
+        im += Q[i * V + bb + j] - Q[j * V + bb + i];
+      }
+    }
+    if constexpr (!CPLX) {
+      M[j * BMAX + i] = re;
+      M[i * BMAX + j] = re;
+    } else {
+      M[2 * (j * BMAX + i)] = re;
+      M[2 * (j * BMAX + i) + 1] = (i == j) ? 0.0 : im;
+      M[2 * (i * BMAX + j)] = re;
+      M[2 * (i * BMAX + j) + 1] = (i == j) ? 0.0 : -im;
+    }
+  }
+  __syncthreads();
+
+  // 2. Choleskys of A-hat and B-hat side by side (pivots on warps 0 and 1)
+  for (int k = 0; k < bb; ++k) {
+    if (threadIdx.x == 0 || threadIdx.x == 32) {
+      const int mat = threadIdx.x >> 5;
+      double* M = mat ? Bm : A;
+      const double dkk = M[E * (k * BMAX + k)];
+      if (!(dkk > 0.0) || !isfinite(dkk)) {
+        s_bad = 1;
+        s_inv[mat] = 0.0;
+      } else {
+        const double inv = rsqrt(dkk);
+        M[E * (k * BMAX + k)] = dkk * inv;
+        s_inv[mat] = inv;
+      }
+    }
+    __syncthreads();
+    if (s_bad) break;
+    const int rem = bb - k - 1;
+    for (int t = threadIdx.x; t < 2 * rem; t += blockDim.x) {
+      const int mat = t >= rem ? 1 : 0;
+      const int j = k + 1 + t - mat * rem;
+      double* M = mat ? Bm : A;
+      const double inv = s_inv[mat];
+      M[E * (j * BMAX + k)] *= inv;
+      if constexpr (CPLX) M[E * (j * BMAX + k) + 1] *= inv;
+    }
+    __syncthreads();
+    const int nrem = rem * (rem + 1) / 2;
+    for (int t = threadIdx.x; t < 2 * nrem; t += blockDim.x) {
+      const int mat = t >= nrem ? 1 : 0;
+      const int ij = s_tri[t - mat * nrem];
+      const int i = k + 1 + (ij & 255), j = k + 1 + (ij >> 8);
+      double* M = mat ? Bm : A;
+      if constexpr (!CPLX) {
+        M[j * BMAX + i] = fma(-M[i * BMAX + k], M[j * BMAX + k], M[j * BMAX + i]);
+      } else {
+        const double kir = M[2 * (i * BMAX + k)], kii = M[2 * (i * BMAX + k) + 1];
+        const double kjr = M[2 * (j * BMAX + k)], kji = M[2 * (j * BMAX + k) + 1];
+        M[2 * (j * BMAX + i)] -= kir * kjr + kii * kji;
+        M[2 * (j * BMAX + i) + 1] -= kir * kji - kii * kjr;
+      }
+    }
+    __syncthreads();
+  }
+  if (s_bad) {
+    if (lead) {
+      b.flags[slot] = 0;
+      atomicAdd(&b.ctr[prm.chol_skip ? 3 : 2], 1ull);
+    }
+    return;  // no shared memory of the peer has been read yet
+  }
+
+  // 3. this CTA's rows [r0, r0 + nr) of F-hat = R_A, G-hat = R_B (upper
+  //    triangular), Z-hat = 0; the prescale z_j = 1/||g-hat_j|| (variant 0)
+  //    from the whole column of R_B, which both CTAs hold
+  const int rh = (bb + 1) / 2;
+  const int ldl = E * rh;
+  const int r0 = rank * rh;
+  const int nr = max(0, min(bb, r0 + rh) - r0);
+  for (int j = warp; j < bb; j += nwarps) {
+    double sq = 0.0;
+    for (int r = lane; r < E * (j + 1); r += 32) {
+      const double v = Bm[E * j * BMAX + r];
+      sq = fma(v, v, sq);
+    }
+    sq = warp_sum(sq);
+    if (lane == 0) th[j] = 1.0 / sqrt(sq);
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < ldl * bb; idx += blockDim.x) {
+    const int j = idx / ldl, rem = idx % ldl, rl = rem / E, pt = rem % E;
+    const int r = r0 + rl;
+    const bool in = rl < nr && r <= j;
+    const double z = th[j];
+    Fl[idx] = in ? A[E * (j * BMAX + r) + pt] * z : 0.0;
+    Gl[idx] = in ? Bm[E * (j * BMAX + r) + pt] * z : 0.0;
+    Zl[idx] = (rl < nr && r == j && pt == 0) ? z : 0.0;
+  }
+  const int M = bb + (bb & 1);
+  const int npairs = M / 2;
+  const double tol = prm.tol > 0.0 ? prm.tol : prm.eps * sqrt((double)bb);
+  for (int idx = threadIdx.x; idx < (M - 1) * npairs; idx += blockDim.x) {
+    int i, j;
+    rr_pair(M, idx / npairs, idx % npairs, i, j);
+    s_pair[idx / npairs][idx % npairs][0] = (unsigned char)i;
+    s_pair[idx / npairs][idx % npairs][1] = (unsigned char)j;
+  }
+  __syncthreads();
+
+  const int hl = lane & 15;
+  int xs = 0;  // exchanges so far: the parity selects the buffer
+  bool exchanged = false;
+  for (int sw = 0; sw < prm.inner_max; ++sw) {
+    for (int st = 0; st < M - 1; ++st, ++xs) {
+      const int buf = xs & 1;
+      // a. partial dot products over this CTA's rows, one pair per half-warp
+      for (int kb = 2 * warp; kb < npairs; kb += 2 * nwarps) {
+        const int k = kb + (lane >> 4);
+        int i = 0, j = 0;
+        bool valid = false;
+        if (k < npairs) {
+          i = s_pair[st][k][0];
+          j = s_pair[st][k][1];
+          valid = j < bb;
+        }
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        double w[4] = {0.0, 0.0, 0.0, 0.0};
+        if (valid && hl < nr) {
+          if constexpr (!CPLX) {
+            const double fi = Fl[i * ldl + hl], fj = Fl[j * ldl + hl];
+            v[0] = fi * fi;
+            v[1] = fj * fj;
+            v[2] = fi * fj;
+            v[3] = Gl[i * ldl + hl] * Gl[j * ldl + hl];
+          } else {
+            const double fir = Fl[i * ldl + 2 * hl], fii = Fl[i * ldl + 2 * hl + 1];
+            const double fjr = Fl[j * ldl + 2 * hl], fji = Fl[j * ldl + 2 * hl + 1];
+            const double gir = Gl[i * ldl + 2 * hl], gii = Gl[i * ldl + 2 * hl + 1];
+            const double gjr = Gl[j * ldl + 2 * hl], gji = Gl[j * ldl + 2 * hl + 1];
+            v[0] = fma(fir, fir, fii * fii);
+            v[1] = fma(fjr, fjr, fji * fji);
+            v[2] = fma(fir, fjr, fii * fji);   // Re(conj(f_i) f_j)
+            v[3] = fma(fir, fji, -fii * fjr);  // Im(conj(f_i) f_j)
+            w[0] = fma(gir, gjr, gii * gji);
+            w[1] = fma(gir, gji, -gii * gjr);
+          }
+        }
+        const double sv = half_sum4(v);
+        double swv = 0.0;
+        if constexpr (CPLX) swv = half_sum4(w);
+        const int q = ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+        if (valid && (lane & 3) == 0) {
+          part[(buf * NPMAX + k) * 8 + q] = sv;
+          if constexpr (CPLX) part[(buf * NPMAX + k) * 8 + 4 + q] = swv;
+        }
+      }
+      // b. the two halves of every dot product meet
+      cluster.sync();
+      exchanged = true;
+      {
+        const double* peer = cluster.map_shared_rank(part, rank ^ 1);
+        constexpr int NV = CPLX ? 6 : 4;
+        for (int t = threadIdx.x; t < npairs * NV; t += blockDim.x) {
+          const int k = t / NV, qq = t % NV;
+          if (s_pair[st][k][1] >= bb) continue;
+          const int off = (buf * NPMAX + k) * 8 + qq;
+          const double tot = part[off] + peer[off];  // a + b = b + a: the same bits in both CTAs
+          double* pk = reinterpret_cast<double*>(&pin[k]);  // a11, a22, ar, ai, br, bi
+          if constexpr (!CPLX) {
+            if (qq < 3) pk[qq] = tot;
+            else { pk[4] = tot; pk[3] = 0.0; pk[5] = 0.0; }
+          } else {
+            pk[qq] = tot;
+          }
+        }
+      }
+      __syncthreads();
+      // c. 2x2 parameters in FP64, one pair per lane (as in the one-CTA kernel)
+      auto count_flags = [&](int fl) {
+        const unsigned rot = __ballot_sync(FULL, fl & PV_ROT), big = __ballot_sync(FULL, fl & PV_BIG);
+        const unsigned bad = __ballot_sync(FULL, fl & PV_FAIL), chg = __ballot_sync(FULL, fl & (PV_ROT | PV_SWAP));
+        if (lane == 0) {
+          s_ctr[0] += __popc(rot);
+          s_ctr[1] += __popc(big);
+          if (bad) s_ctr[2] = 1;
+          if (chg) s_ctr[3] = 1;
+        }
+      };
+      if (warp <= 1) {
+        const bool act = lane < npairs && s_pair[st][lane < npairs ? lane : 0][1] < bb;
+        int fl = 0;
+        PivotOut o;
+        bool have = false;
+        if constexpr (!CPLX) {
+          if (warp == 1) {
+            double xi = 0.0, eta = 0.0;
+            if (act) real_chain_b(pin[lane].br, xi, eta);
+            s_xi[lane] = xi;
+            s_eta[lane] = eta;
+            param_pair_barrier();
+          } else {
+            RealChainA r;
+            double a11 = 0.0, a22 = 0.0, a12 = 0.0, x = 0.0;
+            if (act) {
+              const PivInT<double> pv = pin[lane];
+              a11 = pv.a11; a22 = pv.a22; a12 = pv.ar; x = pv.br;
+              r = real_chain_a(a11, a22, a12, x, tol);
+            }
+            param_pair_barrier();
+            if (act) {
+              o = real_combine(a11, a22, a12, x, r, s_xi[lane], s_eta[lane], prm.sort, prm.f32cls, prm.crit2);
+              have = true;
+            }
+          }
+        } else {
+          if (warp == 0 && act) {
+            const PivInT<double> pv = pin[lane];
+            o = pivot_cplx(pv.a11, pv.a22, pv.ar, pv.ai, pv.br, pv.bi, tol, prm.sort, prm.f32cls, prm.crit2);
+            have = true;
+          }
+        }
+        if (warp == 0) {
+          if (have) {
+            PivZ<double> zq;
+            zq.z11 = o.z11; zq.z12 = o.z12; zq.z21 = o.z21; zq.z22 = o.z22;
+            zq.z12i = CPLX ? o.z12i : 0.0;
+            zq.z21i = CPLX ? o.z21i : 0.0;
+            zq.flags = o.flags;
+            pout[lane] = zq;
+            fl = o.flags;
+          }
+          count_flags(fl);
+        }
+      }
+      __syncthreads();
+      // d. the transformations on this CTA's rows, one pair per half-warp
+      for (int kb = 2 * warp; kb < npairs; kb += 2 * nwarps) {
+        const int k = kb + (lane >> 4);
+        if (k >= npairs || hl >= nr) continue;
+        const int i = s_pair[st][k][0], j = s_pair[st][k][1];
+        if (j >= bb) continue;
+        const PivZ<double> o = pout[k];
+        const bool rot = o.flags & PV_ROT, swp = o.flags & PV_SWAP;
+        if (!rot && !swp) continue;
+        auto upd = [&](double* Y) {
+          if constexpr (!CPLX) {
+            const double yi = Y[i * ldl + hl], yj = Y[j * ldl + hl];
+            double ni = yi, nj = yj;
+            if (rot) {
+              ni = fma(yj, o.z21, yi * o.z11);
+              nj = fma(yi, o.z12, yj * o.z22);
+            }
+            Y[i * ldl + hl] = swp ? nj : ni;
+            Y[j * ldl + hl] = swp ? ni : nj;
+          } else {
+            const double yir = Y[i * ldl + 2 * hl], yii = Y[i * ldl + 2 * hl + 1];
+            const double yjr = Y[j * ldl + 2 * hl], yji = Y[j * ldl + 2 * hl + 1];
+            double nir = yir, nii = yii, njr = yjr, nji = yji;
+            if (rot) {
+              nir = fma(yjr, o.z21, fma(-yji, o.z21i, yir * o.z11));
+              nii = fma(yjr, o.z21i, fma(yji, o.z21, yii * o.z11));
+              njr = fma(yir, o.z12, fma(-yii, o.z12i, yjr * o.z22));
+              nji = fma(yir, o.z12i, fma(yii, o.z12, yji * o.z22));
+            }
+            Y[i * ldl + 2 * hl] = swp ? njr : nir;
+            Y[i * ldl + 2 * hl + 1] = swp ? nji : nii;
+            Y[j * ldl + 2 * hl] = swp ? nir : njr;
+            Y[j * ldl + 2 * hl + 1] = swp ? nii : nji;
+          }
+        };
+        upd(Fl);
+        upd(Gl);
+        upd(Zl);
+      }
+      __syncthreads();
+      if (s_ctr[2]) break;
+    }
+    __syncthreads();
+    const int sweep_all = s_ctr[0];
+    const int fail = s_ctr[2];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (rank == 0) {
+        if (s_ctr[0]) atomicAdd(&b.ctr[0], (unsigned long long)s_ctr[0]);
+        if (s_ctr[1]) atomicAdd(&b.ctr[1], (unsigned long long)s_ctr[1]);
+      }
+      s_ctr[0] = 0;
+      s_ctr[1] = 0;
+    }
+    __syncthreads();
+    if (fail) {
+      if (lead) {
+        b.flags[slot] = 0;
+        atomicAdd(&b.ctr[prm.chol_skip ? 3 : 2], 1ull);
+      }
+      if (exchanged) cluster.sync();
+      return;
+    }
+    if (sweep_all == 0) break;
+  }
+
+  // 5. Theta-tilde: theta_j = (||f-hat_j||^2 + ||g-hat_j||^2)^{-1/2} from the
+  //    two CTAs' partial norms, Z-tilde = Z-hat Theta-tilde on own rows
+  if (s_ctr[3] == 0) {
+    if (lead) b.flags[slot] = 0;
+    if (exchanged) cluster.sync();
+    return;
+  }
+  for (int j = warp; j < bb; j += nwarps) {
+    double sq = 0.0;
+    for (int r = lane; r < E * nr; r += 32) {
+      const double f = Fl[j * ldl + r], g = Gl[j * ldl + r];
+      sq = fma(f, f, fma(g, g, sq));
+    }
+    sq = warp_sum(sq);
+    if (lane == 0) nrm[j] = sq;
+  }
+  cluster.sync();
+  {
+    const double* pn = cluster.map_shared_rank(nrm, rank ^ 1);
+    for (int j = threadIdx.x; j < bb; j += blockDim.x) th[j] = 1.0 / sqrt(nrm[j] + pn[j]);
+  }
+  cluster.sync();  // the peer's norms are read: no further access to its shared memory
+  // 6. this CTA's rows of the real view of Z-tilde (row-major V x V, zero
+  //    padded; CTA 0 also writes the padding rows)
+  double* zt = static_cast<double*>(b.ztil) + (size_t)slot * V * V;
+  for (int idx = threadIdx.x; idx < V * V; idx += blockDim.x) {
+    const int k = idx / V, j = idx % V;
+    const int kk = k < bb ? k : k - bb;  // complex: rows bb.. are the -Im / Re block row
+    const bool pad = k >= E * bb;
+    if (pad ? rank != 0 : (kk < r0 || kk >= r0 + nr)) continue;
+    double val = 0.0;
+    if (!pad) {
+      const int rl = kk - r0;
+      if constexpr (!CPLX) {
+        if (j < bb) val = Zl[j * ldl + rl] * th[j];
+      } else {
+        const bool kr = k < bb, jr = j < bb;
+        const int jj = jr ? j : j - bb;
+        if (jj < bb) {
+          const double zr = Zl[jj * ldl + 2 * rl] * th[jj], zi = Zl[jj * ldl + 2 * rl + 1] * th[jj];
+          if (kr && jr) val = zr;
+          else if (kr && !jr) val = zi;
+          else if (!kr && jr) val = -zi;
+          else val = zr;
+        }
+      }
+    }
+    zt[idx] = val;
+  }
+  if (lead) {
+    b.flags[slot] = 1;
+    atomicAdd(&b.ctr[5], 1ull);
+  }
+}
+
 // --------------------------------------------------------------- apply ----
 template <class T, bool CPLX, int V>
 __global__ void __launch_bounds__(256) k_apply(BlkDims d, BlkBuffers b, int step, int tile0) {
@@ -963,8 +1432,28 @@ cudaError_t apply_v(const BlkDims& d, const BlkBuffers& b, int step, cudaStream_
   }
   return cudaSuccess;
 }
+// the two-CTA pivot step for the FP64 sweeps (GSVD_INNER_CLUSTER=0 selects
+// the one-CTA kernel, for comparisons)
+bool inner_cluster_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("GSVD_INNER_CLUSTER");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
 template <class Ti, class To, bool CPLX, int V>
 cudaError_t inner_v(const BlkDims& d, const BlkBuffers& b, int step, const InnerParams& p, cudaStream_t s) {
+  if constexpr (std::is_same<Ti, double>::value && V <= 32) {
+    if (inner_cluster_enabled()) {
+      const size_t smem2 = inner2_smem<CPLX, V>();
+      auto kern2 = k_inner2<CPLX, V>;
+      cudaError_t e2 = set_smem(kern2, smem2);
+      if (e2 != cudaSuccess) return e2;
+      kern2<<<2 * d.nslots, INNER2_THREADS, smem2, s>>>(d, b, step, p);
+      return cudaGetLastError();
+    }
+  }
   const size_t smem = inner_smem<Ti, CPLX, V>();
   constexpr bool can32 = std::is_same<Ti, float>::value;
   auto kern = (can32 && p.par32) ? k_inner<Ti, To, CPLX, V, can32> : k_inner<Ti, To, CPLX, V, false>;

@@ -337,17 +337,56 @@ cudaError_t launch_gemm_f64_by_f32(int m, int n, bool cplx, const double* A, lon
 }
 
 // X(i, j) <- sf_i X(i, j) + sg_i T(i, j)  (n x n, column-major)
-__global__ void k_rows_combine(int n, double* X, long long ldx, const double* sf, const double* T, long long ldt,
-                               const double* sg) {
+// X <- diag(sf) X + diag(sg) T for n x n matrices (E scalars per element;
+// ldx, ldt in elements): row i of both scaled by real factors
+__global__ void k_rows_combine(int n, int E, double* X, long long ldx, const double* sf, const double* T,
+                               long long ldt, const double* sg) {
   const int j = blockIdx.y;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    X[(size_t)j * ldx + i] = fma(sf[i], X[(size_t)j * ldx + i], sg[i] * T[(size_t)j * ldt + i]);
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < E * n; q += gridDim.x * blockDim.x) {
+    const int i = q / E;
+    X[(size_t)j * E * ldx + q] = fma(sf[i], X[(size_t)j * E * ldx + q], sg[i] * T[(size_t)j * E * ldt + q]);
+  }
 }
 
-cudaError_t launch_rows_combine(int n, double* X, long long ldx, const double* sf, const double* T, long long ldt,
-                                const double* sg, cudaStream_t s) {
-  dim3 grid((n + 255) / 256, n);
-  k_rows_combine<<<grid, 256, 0, s>>>(n, X, ldx, sf, T, ldt, sg);
+cudaError_t launch_rows_combine(int n, bool cplx, double* X, long long ldx, const double* sf, const double* T,
+                                long long ldt, const double* sg, cudaStream_t s) {
+  const int E = cplx ? 2 : 1;
+  dim3 grid((E * n + 255) / 256, n);
+  k_rows_combine<<<grid, 256, 0, s>>>(n, E, X, ldx, sf, T, ldt, sg);
+  return cudaGetLastError();
+}
+
+// C = A^H B for complex A (m x k), B (m x n), C (k x n), interleaved (re, im),
+// leading dimensions in complex elements: 16 x 16 output tiles, 16-row
+// chunks of A and B staged in shared memory (loaded along the columns), each
+// entry summed over the rows in order with FP64 fmas
+__global__ void __launch_bounds__(256) k_gemm_ch(int m, int k, int n, const double2* A, long long lda,
+                                                 const double2* B, long long ldb, double2* C, long long ldc) {
+  __shared__ double2 As[16][17], Bs[16][17];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int c0 = blockIdx.x * 16, d0 = blockIdx.y * 16;
+  double cr = 0.0, ci = 0.0;
+  for (int r0 = 0; r0 < m; r0 += 16) {
+    const int r = r0 + tx;  // consecutive threads read consecutive rows of one column
+    As[tx][ty] = (r < m && c0 + ty < k) ? A[(size_t)(c0 + ty) * lda + r] : make_double2(0.0, 0.0);
+    Bs[tx][ty] = (r < m && d0 + ty < n) ? B[(size_t)(d0 + ty) * ldb + r] : make_double2(0.0, 0.0);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const double2 a = As[q][tx], b = Bs[q][ty];
+      cr = fma(a.x, b.x, fma(a.y, b.y, cr));    // Re(conj(a) b)
+      ci = fma(a.x, b.y, fma(-a.y, b.x, ci));   // Im(conj(a) b)
+    }
+    __syncthreads();
+  }
+  if (c0 + tx < k && d0 + ty < n) C[(size_t)(d0 + ty) * ldc + c0 + tx] = make_double2(cr, ci);
+}
+
+cudaError_t launch_gemm_ch(int m, int k, int n, const double* A, long long lda, const double* B, long long ldb,
+                           double* C, long long ldc, cudaStream_t s) {
+  dim3 grid((k + 15) / 16, (n + 15) / 16);
+  k_gemm_ch<<<grid, 256, 0, s>>>(m, k, n, reinterpret_cast<const double2*>(A), lda,
+                                 reinterpret_cast<const double2*>(B), ldb, reinterpret_cast<double2*>(C), ldc);
   return cudaGetLastError();
 }
 

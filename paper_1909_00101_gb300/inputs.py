@@ -65,6 +65,9 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
+            # threads that wait at a barrier sleep instead of spinning (the
+            # generator may share the cores with other work)
+            os.environ.setdefault("OMP_WAIT_POLICY", "passive")
             lib = ctypes.CDLL(build())
             dp = ctypes.POINTER(ctypes.c_double)
             i64, u64, i32 = ctypes.c_int64, ctypes.c_uint64, ctypes.c_int32
@@ -88,7 +91,12 @@ def _p(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def _threads() -> int:
+def _threads(work: float = 1e12) -> int:
+    """Threads for a job of about `work` multiply-adds: one below 2^24 (the
+    parallel regions would cost more than they save), else every core.  The
+    results do not depend on the thread count."""
+    if work < 2.0 ** 24:
+        return 1
     try:
         return max(1, len(os.sched_getaffinity(0)))
     except AttributeError:
@@ -119,7 +127,7 @@ def haar(seed: int, stream: int, m: int, n: int, cplx: bool = False) -> np.ndarr
     lib = _load()
     g = np.empty(m * n * (2 if cplx else 1))
     lib.ig_gauss(seed, stream, g.size, _p(g))
-    st = lib.ig_orthonormalize(m, n, _p(g), 1 if cplx else 0, _threads())
+    st = lib.ig_orthonormalize(m, n, _p(g), 1 if cplx else 0, _threads(2.0 * m * n * n))
     if st != 0:
         raise RuntimeError("Gram-Schmidt of a Gaussian matrix failed (%d)" % st)
     return _as_matrix(g, m, n, cplx)
@@ -158,7 +166,8 @@ def matmul(a: np.ndarray, b: np.ndarray) -> np.ndarray:
     a = np.asfortranarray(a, dtype=dt)
     b = np.asfortranarray(b, dtype=dt)
     c = np.empty((m, n), dtype=dt, order="F")
-    _load().ig_gemm(m, n, k, _p(_buf(a)), m, _p(_buf(b)), k, _p(_buf(c)), m, 1 if cplx else 0, _threads())
+    _load().ig_gemm(m, n, k, _p(_buf(a)), m, _p(_buf(b)), k, _p(_buf(c)), m, 1 if cplx else 0,
+                    _threads(float(m) * n * k))
     return c
 
 

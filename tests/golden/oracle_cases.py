@@ -29,6 +29,49 @@ for _k, (_mf, _mg, _n) in enumerate(BATCH_SHAPES):
     CASES["batch_real_%d" % _k] = dict(mf=_mf, mg=_mg, n=_n, lo=1e-3, hi=1e3, cond=1e2, cplx=False, seed=1000 + _k)
 
 
+# pairs of the GPU parity tests whose oracle run is slow where long double is
+# the 128-bit software format (AArch64): stored once, found by their SHA-256
+_T = dict(lo=1e-3, hi=1e3, cond=1e2)
+CASES.update({
+    "t_autotune_600x500x256": dict(mf=600, mg=500, n=256, lo=1e-2, hi=1e2, cond=1e2, cplx=False, seed=17),
+    "t_shortened_mixed_700x600x192": dict(mf=700, mg=600, n=192, lo=1e-4, hi=1e4, cond=1e3, cplx=False, seed=31),
+    "t_shortened_512x400x160": dict(mf=512, mg=400, n=160, cplx=False, seed=160, **_T),
+    "t_shortened_333x1000x97": dict(mf=333, mg=1000, n=97, cplx=False, seed=97, **_T),
+    "t_shortened_2000x150x129": dict(mf=2000, mg=150, n=129, cplx=False, seed=129, **_T),
+    "t_mixed_200x160x128": dict(mf=200, mg=160, n=128, cplx=False, seed=21, **_T),
+    "t_mixed_cplx_200x160x128": dict(mf=200, mg=160, n=128, cplx=True, seed=21, **_T),
+    "t_mixed_p32_200x160x128": dict(mf=200, mg=160, n=128, cplx=False, seed=22, **_T),
+    "t_mixed_p32_cplx_200x160x128": dict(mf=200, mg=160, n=128, cplx=True, seed=22, **_T),
+    "t_blocked_w32_300x257x150": dict(mf=300, mg=257, n=150, cplx=False, seed=182, **_T),
+    "t_blocked_w16_200x180x100": dict(mf=200, mg=180, n=100, cplx=False, seed=116, **_T),
+    "t_right_300x260x128": dict(mf=300, mg=260, n=128, cplx=False, seed=131, **_T),
+    "t_serving_300x280x160": dict(mf=300, mg=280, n=160, lo=1e-2, hi=1e2, cond=1e2, cplx=False, seed=204),
+    "t_serving_200x150x100": dict(mf=200, mg=150, n=100, lo=1e-2, hi=1e2, cond=1e2, cplx=False, seed=201),
+    "t_serving_cplx_90x80x70": dict(mf=90, mg=80, n=70, lo=1e-2, hi=1e2, cond=1e2, cplx=True, seed=202),
+})
+for _w in (4, 8, 16):
+    CASES["t_blocked_cplx_w%d_120x90x72" % _w] = dict(mf=120, mg=90, n=72, cplx=True, seed=_w, **_T)
+
+
+def by_sha256() -> dict:
+    """{sha256 of a pair: case} over the stored records (read once)."""
+    global _INDEX
+    if _INDEX is None:
+        _INDEX = {}
+        for c in CASES:
+            try:
+                with open(path(c)) as f:
+                    head = f.read(4096)
+                i = head.index('"sha256"')
+                _INDEX[head[i:].split('"')[3]] = c
+            except (OSError, ValueError, IndexError):
+                pass
+    return _INDEX
+
+
+_INDEX = None
+
+
 def path(case: str) -> str:
     return os.path.join(HERE, "oracle_sigma_%s.json" % case)
 

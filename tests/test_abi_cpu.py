@@ -89,13 +89,18 @@ def test_invalid_problems_rejected_before_any_launch(lib):
     # a class that runs on the pointwise kernel has nothing to tune
     assert lib.gsvd_autotune(h, 0, ctypes.c_int64(100), ctypes.c_int64(100), ctypes.c_int64(32), ctypes.byref(w)) == 0
     assert w.value == 0
-    # right vectors: real problems only, ld >= n
+    # right vectors: ld >= n
     X = np.zeros((4, 4), order="F")
     p.X, p.ldx = X.ctypes.data, 3
     assert lib.gsvd_solve(h, ctypes.byref(p), ctypes.byref(info)) == hz.EINVAL
-    p.ldx, p.dtype = 4, 1
-    assert lib.gsvd_solve(h, ctypes.byref(p), ctypes.byref(info)) == hz.EINVAL
+    assert info.status == hz.EINVAL
     assert lib.gsvd_destroy(h) == 0
+    # a negative timeout is refused at creation
+    c = hz.Config()
+    lib.gsvd_config_default(ctypes.byref(c))
+    c.timeout_ms = -1
+    h2 = ctypes.c_void_p()
+    assert lib.gsvd_create(ctypes.byref(h2), ctypes.byref(c), None) == hz.EINVAL
 
 
 def test_bad_config_rejected(lib):

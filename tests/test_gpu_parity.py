@@ -62,7 +62,11 @@ def _np(t):
 
 def stored_or_live(p_F, p_G, case=None):
     """(sigma_fp64, sigma_ext) of the oracle: the stored values of a case
-    (after the check that the pair is the stored one), else computed now."""
+    (after the check that the pair is the stored one; without a case name,
+    a stored record of the same bytes if there is one), else computed now."""
+    if case is None:
+        from paper_1909_00101_gb300.inputs import sha256
+        case = oracle_cases.by_sha256().get(sha256(p_F, p_G))
     if case is not None:
         rec = oracle_cases.load_checked(case, p_F, p_G)
         assert rec["status_fp64"] == 0 and rec["status_ext"] == 0
@@ -274,6 +278,22 @@ def test_right_vectors(hz, kw, shape):
     check(p.F, p.G, r, label="right vectors %s" % (kw,))
 
 
+@pytest.mark.parametrize("kw", [dict(path="pointwise"), dict(path="blocked", block_w=8),
+                                dict(path="blocked", block_w=8, precision="mixed")])
+def test_right_vectors_complex(hz, kw):
+    """X = Z^-1 for complex pairs: X = Sigma_F U^* F + Sigma_G V^* G."""
+    n = 40 if kw["path"] == "pointwise" else 72
+    p = make_pair(2 * n, n + 10, n, lo=1e-3, hi=1e3, cond=1e2, cplx=True, seed=n + 9)
+    r = hz.solve(_dev(p.F), _dev(p.G), right_vectors=True, **kw)
+    assert r.status == 0, r.info
+    X, Z = _np(r.X), _np(r.Z)
+    err = np.max(np.abs(X @ Z - np.eye(n))) / (np.linalg.norm(X, 2) * np.linalg.norm(Z, 2))
+    assert err <= 64 * n * 2.0 ** -53, err
+    Zi = np.linalg.inv(Z)
+    assert np.max(np.abs(X - Zi)) / np.max(np.abs(Zi)) <= 1e-9
+    check(p.F, p.G, r, label="complex right vectors %s" % (kw,))
+
+
 def test_right_vectors_not_in_batched_calls(hz):
     """Batched calls reject a problem that asks for X (per-problem status)."""
     import ctypes
@@ -403,6 +423,55 @@ def test_serving_results_equal_alone_and_in_mix(hz):
 
 
 # ---------------------------------------------------------------- status ----
+
+def test_timeout_stops_at_a_sweep_boundary_with_valid_outputs(hz):
+    """timeout_ms: once the deadline has passed no further sweep is issued;
+    the status is ETIMEOUT, the outputs are a finalised decomposition of the
+    pair at that point, and the handle serves the next solve normally."""
+    p = make_pair(3000, 2500, 512, lo=1e-4, hi=1e4, cond=1e3, seed=71)
+    with hz.Solver(path="blocked", block_w=16, shorten=0, inner_max_sweeps=1, max_sweeps=60,
+                   timeout_ms=1) as s:
+        r = s.solve(_dev(p.F), _dev(p.G))
+    assert r.status == hz.ETIMEOUT, r.info
+    assert r.info["sweeps_fp64"] == 1, r.info
+    inv = invariants(p.F, p.G, _np(r.U), _np(r.V), _np(r.Z), _np(r.sigma_f), _np(r.sigma_g), _np(r.sigma))
+    assert inv["FZ"] < 1e-12 and inv["GZ"] < 1e-12 and inv["scale"] <= 8 * 2.0 ** -53, inv
+    with hz.Solver(path="blocked", block_w=16, shorten=0, inner_max_sweeps=1, max_sweeps=60,
+                   timeout_ms=600000) as s:
+        r2 = s.solve(_dev(p.F), _dev(p.G))
+    assert r2.status == 0 and r2.info["sweeps_fp64"] > 1, r2.info
+
+
+def test_serving_workspaces_come_back_to_the_pool(hz):
+    """Served requests take their workspaces from the handle's stream-ordered
+    pool and give them back: after a first round of requests, further rounds
+    of the same sizes reserve no more device memory."""
+    import time
+    shapes = [(300, 280, 160), (200, 150, 100), (600, 500, 256), (90, 80, 70)]
+    pairs = [make_pair(*sh, seed=500 + k) for k, sh in enumerate(shapes)]
+    dev = [(_dev(p.F), _dev(p.G)) for p in pairs]
+
+    def round_trip(s):
+        tickets = [s.submit(F, G) for F, G in dev]
+        done, t0 = set(), time.time()
+        while len(done) < len(tickets) and time.time() - t0 < 120:
+            for k, (t, _) in enumerate(tickets):
+                if k not in done and s.poll(t)[0] != hz.EAGAIN:
+                    done.add(k)
+            time.sleep(0.001)
+        assert len(done) == len(tickets)
+        torch.cuda.synchronize()
+
+    with hz.Solver(max_inflight=4) as s:
+        round_trip(s)
+        free0 = torch.cuda.mem_get_info()[0]
+        for _ in range(3):
+            round_trip(s)
+        free1 = torch.cuda.mem_get_info()[0]
+    # (a small slack for torch's own caching allocator, which holds the
+    # requests' output buffers)
+    assert free1 >= free0 - (32 << 20), (free0, free1)
+
 
 def test_status_nonfinite_input(hz):
     p = make_pair(40, 40, 20, seed=1)
