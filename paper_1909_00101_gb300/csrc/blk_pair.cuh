@@ -30,4 +30,24 @@ __device__ __forceinline__ bool load_pair(const BlkDims& d, const BlkBuffers& b,
   return true;
 }
 
+// The CTA's problem and pair slot: in a one-problem launch the slot is the
+// grid-x index and d, b (and prm) are the kernel's own; in a batched launch
+// they come from the item's problem.  False: nothing to do in this launch.
+__device__ __forceinline__ bool batch_item(const BlkBatch& bt, int xi, int step, BlkDims& d, BlkBuffers& b,
+                                           int& slot, InnerParams* prm = nullptr) {
+  if (!bt.probs) {
+    slot = xi;
+    return true;
+  }
+  const int2 it = bt.items[xi];
+  if (!(bt.sweep[it.x].state & (1 << bt.phase))) return false;
+  const BlkProb& P = bt.probs[it.x];
+  if (step >= P.steps) return false;
+  d = P.d[bt.phase];
+  b = P.b[bt.phase];
+  if (prm) *prm = P.ip[bt.phase];
+  slot = it.y;
+  return true;
+}
+
 }  // namespace hz

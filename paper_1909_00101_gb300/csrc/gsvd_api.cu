@@ -901,6 +901,331 @@ int solve_any(const gsvd_config& cfg, const gsvd_problem* p, gsvd_info* info, De
   return dev ? solve_device(cfg, p, info, ws, h_ctr, s) : solve_host(cfg, p, info, ws, h_ctr, s);
 }
 
+// The blocked problems of a gsvd_solve_batched call, all advancing together
+// (north of the one-problem loop of Alg. cpu1): a global sweep runs, for every
+// group of problems with the same data type and real-view width V, the outer
+// steps k = 0, 1, ... as one Gram, one pivot-step and one apply launch each
+// over all (problem, pair) items of the group -- a problem with fewer steps
+// per sweep, or one not sweeping in that precision, has its CTAs leave at
+// once -- then one launch for every problem's convergence test, one for the
+// rescales, and one copy of the problems' states to the host.  The launches
+// of a global sweep do not depend on the problem count; from the second
+// sweep on they replay as one captured CUDA graph.  Mixed precision: every
+// problem runs its FP32 bulk sweeps, the restart F <- F Z_acc (one batched
+// launch sequence for the problems that reach it in the same sweep), and its
+// FP64 sweeps, with the same rules as a single solve.  Every problem's
+// arithmetic is the single-solve kernels' own, so a problem gets the same
+// bits as gsvd_solve of it with shortening off.  The batched path does not
+// shorten (the QR shortening of Sec. 2 is a per-problem phase).
+struct BatchGroup {
+  bool cplx = false;
+  int V = 0, w = 0;
+  int steps = 0;                 // most outer steps per sweep in the group
+  int gy_gram[2] = {0, 0};       // grid y of the Gram per phase
+  int gy_apply = 0;              // grid y of the apply
+  int item0 = 0, nitems = 0;     // (problem, slot) items of the group
+  InnerParams ip[2];
+  bool oz = false;               // FP64 Gram and apply on the tensor cores
+};
+
+// A stream owned for the duration of a call, ordered after the work already
+// queued on another stream (the handle's, which may be the legacy stream,
+// where no graph can be captured).
+struct OwnStream {
+  cudaStream_t s = nullptr;
+  explicit OwnStream(cudaStream_t after) {
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      s = nullptr;
+      return;
+    }
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) {
+      cudaEventRecord(e, after);
+      cudaStreamWaitEvent(s, e, 0);
+      cudaEventDestroy(e);
+    }
+  }
+  ~OwnStream() {
+    if (s) {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+  }
+  OwnStream(const OwnStream&) = delete;
+  OwnStream& operator=(const OwnStream&) = delete;
+};
+
+int solve_blocked_batch(gsvd_ctx* h, const gsvd_problem* ps, const std::vector<int>& idx, gsvd_info* infos,
+                        cudaStream_t hs_stream) {
+  TraceRange phase("gsvd batched sweeps");
+  const int P = (int)idx.size();
+  if (P == 0) return GSVD_OK;
+  OwnStream own(hs_stream);
+  if (!own.s) return GSVD_ECUDA;
+  const cudaStream_t s = own.s;
+  const bool mixed = h->cfg.precision == GSVD_PREC_MIXED;
+  std::vector<Plan> plans(P);
+  std::vector<gsvd_config> cfgs(P);
+  std::vector<size_t> woff(P);
+  size_t wtotal = 0;
+  int maxm = 1, maxn = 1;
+  for (int k = 0; k < P; ++k) {
+    const gsvd_problem& p = ps[idx[k]];
+    cfgs[k] = cfg_for(h, &p);
+    cfgs[k].shorten = 0;
+    if (!make_plan(cfgs[k], p.dtype, p.m_f, p.m_g, p.n, plans[k])) return GSVD_EINVAL;
+    woff[k] = wtotal;
+    wtotal += align256(plans[k].total);
+    maxm = std::max({maxm, (int)p.m_f, (int)p.m_g});
+    maxn = std::max(maxn, (int)p.n);
+  }
+  // groups by (data type, V)
+  std::map<std::pair<int, int>, std::vector<int>> gmap;
+  for (int k = 0; k < P; ++k) gmap[{plans[k].cplx ? 1 : 0, plans[k].V}].push_back(k);
+  std::vector<BatchGroup> groups;
+  std::vector<int2> items;
+  for (auto& kv : gmap) {
+    BatchGroup g;
+    g.cplx = kv.first.first != 0;
+    g.V = kv.first.second;
+    g.w = plans[kv.second[0]].w;
+    g.oz = h->cfg.fp64_gemm == 1 && oz_supported(g.V);
+    g.item0 = (int)items.size();
+    for (int k : kv.second) {
+      const Plan& Pk = plans[k];
+      g.steps = std::max(g.steps, Pk.steps);
+      g.gy_gram[0] = std::max(g.gy_gram[0], Pk.rf32 + Pk.rg32);
+      g.gy_gram[1] = std::max(g.gy_gram[1], g.oz ? Pk.rf32 + Pk.rg32 : Pk.rf + Pk.rg);
+      g.gy_apply = std::max(g.gy_apply, (Pk.mf + 63) / 64 + (Pk.mg + 63) / 64 + (Pk.n + 63) / 64);
+      for (int sl = 0; sl < Pk.nslots; ++sl) items.push_back(make_int2(k, sl));
+    }
+    g.nitems = (int)items.size() - g.item0;
+    if (g.gy_apply > 65535) return GSVD_ETOOBIG;
+    groups.push_back(g);
+  }
+  // the tables: problems, column data, items, round-robin tables, states
+  const size_t o_prob = 0;
+  const size_t o_col = o_prob + align256(sizeof(BlkProb) * P);
+  const size_t o_item = o_col + align256(sizeof(BatchCol) * P);
+  const size_t o_sw = o_item + align256(sizeof(int2) * items.size());
+  size_t o_tab = o_sw + align256(sizeof(BatchSweep) * P);
+  std::vector<size_t> toff(P);
+  size_t tb = 0;
+  std::vector<std::vector<uint16_t>> tabs(P);
+  for (int k = 0; k < P; ++k) {
+    tabs[k] = round_robin_table(plans[k].neff);
+    toff[k] = tb;
+    tb += align256(tabs[k].size() * 2);
+  }
+  const size_t tbytes = o_tab + tb;
+  DevBuf buf;
+  CK(buf.ensure(tbytes + wtotal, s));
+  unsigned char* base = static_cast<unsigned char*>(buf.p);
+  unsigned char* wbase = base + tbytes;
+  std::vector<unsigned char> host(o_sw);
+  BlkProb* hp = reinterpret_cast<BlkProb*>(host.data() + o_prob);
+  BatchCol* hc = reinterpret_cast<BatchCol*>(host.data() + o_col);
+  std::memcpy(host.data() + o_item, items.data(), sizeof(int2) * items.size());
+  for (int k = 0; k < P; ++k) {
+    const gsvd_problem& p = ps[idx[k]];
+    const Plan& Pk = plans[k];
+    const gsvd_config& c = cfgs[k];
+    unsigned char* w = wbase + woff[k];
+    BlkProb bp;
+    std::memset(&bp, 0, sizeof bp);
+    for (int ph = 0; ph < 2; ++ph) {
+      const bool fp32 = ph == 0;
+      BlkDims& d = bp.d[ph];
+      d.mf = Pk.mf; d.mg = Pk.mg; d.n = Pk.n; d.w = Pk.w; d.nblk = Pk.nblk; d.nslots = Pk.nslots;
+      const bool oz = !fp32 && c.fp64_gemm == 1 && oz_supported(Pk.V);
+      d.rf = (fp32 || oz) ? Pk.rf32 : Pk.rf;
+      d.rg = (fp32 || oz) ? Pk.rg32 : Pk.rg;
+      d.trows = 64;
+      BlkBuffers& b = bp.b[ph];
+      if (fp32) {
+        b.F = w + Pk.off_f32; b.ldf = Pk.mf;
+        b.G = w + Pk.off_g32; b.ldg = Pk.mg;
+        b.Z = w + Pk.off_z32; b.ldz = Pk.n;
+      } else {
+        b.F = p.F; b.ldf = p.ldf; b.G = p.G; b.ldg = p.ldg; b.Z = p.Z; b.ldz = p.ldz;
+      }
+      b.partial = w + Pk.off_partial;
+      b.ztil = w + Pk.off_ztil;
+      b.flags = reinterpret_cast<int*>(w + Pk.off_flags);
+      b.ctr = reinterpret_cast<unsigned long long*>(w + Pk.off_ctr);
+      b.table = reinterpret_cast<const uint16_t*>(base + o_tab + toff[k]);
+      InnerParams& ip = bp.ip[ph];
+      ip.eps = fp32 ? EPS32 : EPS64;
+      ip.tol = fp32 ? EPS32 * std::sqrt((double)std::max(Pk.mf, Pk.mg)) : 0.0;
+      ip.inner_max = fp32 && c.inner_max_sweeps_fp32 > 0 ? c.inner_max_sweeps_fp32 : c.inner_max_sweeps;
+      ip.sort = c.sort != 0;
+      ip.f32cls = fp32;
+      ip.crit2 = c.criterion == 2;
+      ip.chol_skip = fp32;
+      ip.par32 = fp32 && c.fp32_params != 0;
+    }
+    bp.steps = Pk.steps;
+    bp.tiles = (Pk.mf + 63) / 64 + (Pk.mg + 63) / 64 + (Pk.n + 63) / 64;
+    hp[k] = bp;
+    BatchCol bc;
+    std::memset(&bc, 0, sizeof bc);
+    bc.mf = Pk.mf; bc.mg = Pk.mg; bc.n = Pk.n; bc.cplx = Pk.cplx ? 1 : 0; bc.w = Pk.w;
+    bc.F = (double*)p.F; bc.ldf = p.ldf; bc.G = (double*)p.G; bc.ldg = p.ldg; bc.Z = (double*)p.Z; bc.ldz = p.ldz;
+    bc.sf = p.sigma_f; bc.sg = p.sigma_g; bc.sigma = p.sigma;
+    if (mixed) {
+      bc.F32 = reinterpret_cast<float*>(w + Pk.off_f32);
+      bc.G32 = reinterpret_cast<float*>(w + Pk.off_g32);
+      bc.Z32 = reinterpret_cast<float*>(w + Pk.off_z32);
+    }
+    bc.zdiag = reinterpret_cast<double*>(w + Pk.off_zdiag);
+    bc.norms = reinterpret_cast<double*>(w + Pk.off_norms);
+    bc.rank = reinterpret_cast<int*>(w + Pk.off_rank);
+    bc.work = reinterpret_cast<double*>(w + Pk.off_work);
+    bc.status = reinterpret_cast<int*>(w + Pk.off_status);
+    bc.ctr = reinterpret_cast<unsigned long long*>(w + Pk.off_ctr);
+    hc[k] = bc;
+  }
+  for (auto& g : groups) {
+    const int k0 = items[g.item0].x;
+    g.ip[0] = hp[k0].ip[0];
+    g.ip[1] = hp[k0].ip[1];
+  }
+  std::vector<uint16_t> htab(tb / 2, 0);
+  for (int k = 0; k < P; ++k) std::memcpy(htab.data() + toff[k] / 2, tabs[k].data(), tabs[k].size() * 2);
+  CK(cudaMemcpyAsync(base, host.data(), o_sw, cudaMemcpyHostToDevice, s));
+  if (tb) CK(cudaMemcpyAsync(base + o_tab, htab.data(), tb, cudaMemcpyHostToDevice, s));
+  const BlkProb* d_prob = reinterpret_cast<const BlkProb*>(base + o_prob);
+  const BatchCol* d_col = reinterpret_cast<const BatchCol*>(base + o_col);
+  const int2* d_item = reinterpret_cast<const int2*>(base + o_item);
+  BatchSweep* d_sw = reinterpret_cast<BatchSweep*>(base + o_sw);
+  BatchRule rule;
+  rule.cap[0] = h->cfg.fp32_max_sweeps;
+  rule.cap[1] = h->cfg.max_sweeps;
+  rule.stop_permille = h->cfg.fp32_stop_permille;
+  rule.inner_max32 = h->cfg.inner_max_sweeps_fp32 > 0 ? h->cfg.inner_max_sweeps_fp32 : h->cfg.inner_max_sweeps;
+  SolveEvents ev;
+  cudaEventRecord(ev.e0, s);
+  CK(launch_batch_init(d_col, d_sw, P, maxm, maxn, mixed, s));
+  if (mixed && rule.cap[0] <= 0) CK(launch_batch_stop(d_sw, P, GSVD_OK, s));  // no FP32 sweeps: straight to the restart
+
+  // one global sweep: every group's outer steps in both precisions, then the
+  // convergence tests and the rescales
+  auto sweep = [&]() -> cudaError_t {
+    cudaError_t e = launch_batch_sweep_begin(d_col, d_sw, P, s);
+    for (int ph = mixed ? 0 : 1; ph < 2 && e == cudaSuccess; ++ph) {
+      const bool fp32 = ph == 0;
+      for (const BatchGroup& g : groups) {
+        BlkBatch bt;
+        bt.probs = d_prob;
+        bt.items = d_item + g.item0;
+        bt.sweep = d_sw;
+        bt.phase = ph;
+        BlkDims dd;
+        std::memset(&dd, 0, sizeof dd);
+        dd.w = g.w;
+        BlkBuffers bb;
+        std::memset(&bb, 0, sizeof bb);
+        const bool oz = !fp32 && g.oz;
+        for (int k = 0; k < g.steps && e == cudaSuccess; ++k) {
+          e = oz ? launch_gram_oz(dd, bb, g.cplx, k, s, &bt, g.nitems, g.gy_gram[ph])
+                 : launch_gram(dd, bb, g.cplx, fp32, k, s, &bt, g.nitems, g.gy_gram[ph]);
+          if (e == cudaSuccess) e = launch_inner(dd, bb, g.cplx, fp32, k, g.ip[ph], s, &bt, g.nitems);
+          if (e == cudaSuccess)
+            e = oz ? launch_apply_oz(dd, bb, g.cplx, k, s, &bt, g.nitems, g.gy_apply)
+                   : launch_apply(dd, bb, g.cplx, fp32, k, s, &bt, g.nitems, g.gy_apply);
+        }
+      }
+    }
+    if (e == cudaSuccess) e = launch_batch_sweep_end(d_col, d_sw, rule, P, s);
+    if (e == cudaSuccess) e = launch_batch_rescale(d_col, d_sw, P, maxn, s);
+    return e;
+  };
+  std::vector<BatchSweep> hs(P);
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  struct GraphGuard {
+    cudaGraph_t& g;
+    cudaGraphExec_t& x;
+    ~GraphGuard() {
+      if (x) cudaGraphExecDestroy(x);
+      if (g) cudaGraphDestroy(g);
+    }
+  } gguard{graph, gexec};
+  bool use_graph = std::getenv("GSVD_BATCH_GRAPH") == nullptr || std::getenv("GSVD_BATCH_GRAPH")[0] != '0';
+  int nsweeps = 0;
+  for (;;) {
+    if (nsweeps == 1 && use_graph) {
+      // the launches of a global sweep never change: capture them once
+      if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        const cudaError_t e = sweep();
+        const cudaError_t ec = cudaStreamEndCapture(s, &graph);
+        if (e != cudaSuccess || ec != cudaSuccess || cudaGraphInstantiate(&gexec, graph, 0) != cudaSuccess) {
+          cudaGetLastError();
+          if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+          if (graph) { cudaGraphDestroy(graph); graph = nullptr; }
+          use_graph = false;
+        }
+      } else {
+        cudaGetLastError();
+        use_graph = false;
+      }
+    }
+    if (gexec) {
+      CK(cudaGraphLaunch(gexec, s));
+    } else {
+      CK(sweep());
+    }
+    ++nsweeps;
+    CK(cudaMemcpyAsync(hs.data(), d_sw, sizeof(BatchSweep) * P, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (deadline_passed()) {
+      CK(launch_batch_stop(d_sw, P, GSVD_ETIMEOUT, s));
+      CK(cudaMemcpyAsync(hs.data(), d_sw, sizeof(BatchSweep) * P, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+    }
+    bool restart = false, active = false;
+    for (const BatchSweep& t : hs) {
+      restart = restart || (t.state & BST_RESTART);
+      active = active || (t.state & (BST_FP32 | BST_FP64));
+    }
+    if (restart) CK(launch_batch_restart(d_col, d_sw, P, maxm, maxn, s));
+    if (!active && !restart) break;
+    if (!active) {  // restarts only: they may start FP64 sweeps
+      CK(cudaMemcpyAsync(hs.data(), d_sw, sizeof(BatchSweep) * P, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      bool any = false;
+      for (const BatchSweep& t : hs) any = any || (t.state & (BST_FP32 | BST_FP64));
+      if (!any) break;
+    }
+  }
+  TraceRange phase_fin("gsvd finalize");
+  CK(launch_batch_finalize(d_col, d_sw, P, maxm, maxn, s));
+  cudaEventRecord(ev.e2, s);
+  CK(cudaMemcpyAsync(hs.data(), d_sw, sizeof(BatchSweep) * P, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ev.e0, ev.e2);
+  for (int k = 0; k < P; ++k) {
+    gsvd_info& in = infos[idx[k]];
+    const BatchSweep& t = hs[k];
+    in.status = t.status;
+    in.sweeps_fp32 = t.sweeps[0];
+    in.sweeps_fp64 = t.sweeps[1];
+    in.transf_all = t.tall;
+    in.transf_big = t.tbig;
+    in.visits = t.visits;
+    in.visits_applied = t.visits_applied;
+    in.visits_fp32 = t.visits32;
+    in.visits_applied_fp32 = t.applied32;
+    in.chol_skipped = t.chol_skipped;
+    in.path = GSVD_PATH_BLOCKED;
+    in.block_w = plans[k].w;
+    in.t_total_us = ms * 1e3;  // the whole batched solve: its problems run together
+  }
+  return GSVD_OK;
+}
+
 void worker_loop(gsvd_ctx* h) {
   cudaStream_t s;
   cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
@@ -1088,41 +1413,47 @@ int gsvd_solve_batched(gsvd_handle h, const gsvd_problem* ps, int32_t count, gsv
     (P.path == GSVD_PATH_POINTWISE ? pw : blk).push_back(k);
   }
   int first = GSVD_OK;
-  // problems on the blocked path run concurrently: a pool of host workers,
-  // each with its own stream and workspace, takes problems in index order
-  // (results do not depend on which worker solves a problem)
-  std::atomic<int> next(0);
-  const int nworkers = std::min<int>((int)blk.size(), h->cfg.max_inflight);
-  std::vector<std::thread> pool;
-  for (int t = 0; t < nworkers; ++t)
-    pool.emplace_back([&]() {
-      cudaStream_t s;
-      if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return;
-      {
-        CallScope call(h->pool, h->cfg.timeout_ms);
-        DevBuf ws;
-        unsigned long long* hc = nullptr;
-        if (cudaMallocHost(&hc, NCTR * sizeof(unsigned long long)) == cudaSuccess) {
-          for (int q = next.fetch_add(1); q < (int)blk.size(); q = next.fetch_add(1)) {
-            gsvd_info& in = loc[blk[q]];
-            const int st = solve_device(cfg_for(h, &ps[blk[q]]), &ps[blk[q]], &in, ws, hc, s);
-            if (st != GSVD_OK && in.status == GSVD_OK) in.status = st;
-          }
-          cudaFreeHost(hc);
-        }
-        ws.release();
-      }
-      cudaStreamSynchronize(s);
-      cudaStreamDestroy(s);
-    });
+  // the blocked problems advance together (solve_blocked_batch) on the
+  // handle's stream; the pointwise ones run meanwhile in one launch on a
+  // stream of their own
+  CallScope call(h->pool, h->cfg.timeout_ms);
+  std::thread pw_thread;
   if (!pw.empty()) {
-    int st = solve_pointwise(h->cfg, ps, pw.data(), (int)pw.size(), h->stream, loc.data());
+    // the pointwise launch on a stream of its own, from a host thread, so that
+    // it overlaps the blocked sweeps; it starts after the work already queued
+    // on the handle's stream
+    cudaEvent_t ready = nullptr;
+    if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) == cudaSuccess) cudaEventRecord(ready, h->stream);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    pw_thread = std::thread([&, ready, dev]() {
+      cudaSetDevice(dev);
+      CallScope pcall(h->pool, 0);
+      cudaStream_t ps_stream = nullptr;
+      int st = GSVD_ECUDA;
+      if (cudaStreamCreateWithFlags(&ps_stream, cudaStreamNonBlocking) == cudaSuccess) {
+        if (ready) cudaStreamWaitEvent(ps_stream, ready, 0);
+        st = solve_pointwise(h->cfg, ps, pw.data(), (int)pw.size(), ps_stream, loc.data());
+        cudaStreamSynchronize(ps_stream);
+        cudaStreamDestroy(ps_stream);
+      }
+      if (st != GSVD_OK)
+        for (int k : pw) loc[k].status = st;
+    });
+    if (!blk.empty()) {
+      const int st = solve_blocked_batch(h, ps, blk, loc.data(), h->stream);
+      if (st != GSVD_OK)
+        for (int k : blk)
+          if (loc[k].status == GSVD_OK) loc[k].status = st;
+    }
+    pw_thread.join();
+    if (ready) cudaEventDestroy(ready);
+  } else if (!blk.empty()) {
+    const int st = solve_blocked_batch(h, ps, blk, loc.data(), h->stream);
     if (st != GSVD_OK)
-      for (int k : pw) loc[k].status = st;
+      for (int k : blk)
+        if (loc[k].status == GSVD_OK) loc[k].status = st;
   }
-  for (auto& t : pool) t.join();
-  for (int k : blk)
-    if (loc[k].status == GSVD_OK && loc[k].path == 0) loc[k].status = GSVD_ECUDA;  // a worker could not start
   for (int k = 0; k < count; ++k)
     if (loc[k].status != GSVD_OK && first == GSVD_OK) first = loc[k].status;
   if (infos) std::memcpy(infos, loc.data(), sizeof(gsvd_info) * count);

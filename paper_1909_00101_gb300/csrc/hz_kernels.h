@@ -88,18 +88,91 @@ struct InnerParams {
   bool par32;          // FP32 bulk sweeps: 2x2 parameters in FP32 (else FP64)
 };
 
+// Batched sweeps (gsvd_solve_batched): many blocked problems advance one
+// outer step per launch.  Grid x enumerates (problem, pair slot) items of all
+// problems of a group (same data type and real-view width V); each CTA loads
+// its problem's dimensions, buffers and pivot-step parameters from the device
+// table and leaves at once when its problem is not sweeping in this phase or
+// has fewer outer steps per sweep than the step being run.  Every problem's
+// arithmetic is the one-problem kernels' own.
+// Progress of one problem of a batched solve (device, read by the host after
+// every global sweep).  State bits: sweeping in the FP32 bulk or the FP64
+// phase, waiting for the restart of the mixed path (F <- F Z_acc ...), a
+// rescale due before the next sweep, the sweep cap reached.
+enum : int { BST_FP32 = 1, BST_FP64 = 2, BST_RESTART = 4, BST_RESCALE = 8, BST_CAP = 16 };
+struct BatchSweep {
+  int state;                   // BST_* bits; 0 = finished
+  int status;
+  int sweeps[2];               // FP32 bulk and FP64 sweeps done
+  int chol_skipped, pad;
+  unsigned long long tall, tbig, visits, visits_applied, visits32, applied32;
+};
+struct BlkProb {
+  BlkDims d[2];         // [0] FP32 bulk sweeps, [1] FP64 sweeps
+  BlkBuffers b[2];
+  InnerParams ip[2];
+  int steps;            // outer steps per sweep
+  int tiles;            // row tiles of the apply over F, G and Z
+};
+struct BlkBatch {
+  const BlkProb* probs = nullptr;  // device table; nullptr: one problem, given by value
+  const int2* items = nullptr;     // device: (problem, slot) of each grid-x index
+  const BatchSweep* sweep = nullptr;  // device: per problem, bit `phase` of its state set while it sweeps in that phase
+  int phase = 0;                   // 0 = FP32 bulk sweeps, 1 = FP64 sweeps
+};
+
+// Column data of one problem of a batched solve (device table): the caller's
+// FP64 data and outputs, the FP32 copies of the mixed-precision path and the
+// problem's workspace.
+struct BatchCol {
+  int mf, mg, n, cplx, w;
+  double* F;
+  long long ldf;
+  double* G;
+  long long ldg;
+  double* Z;
+  long long ldz;
+  double *sf, *sg, *sigma;
+  float *F32, *G32, *Z32;      // mixed precision (ld = mf, mg, n)
+  double* zdiag;
+  double* norms;
+  int* rank;
+  double* work;
+  int* status;                 // [0]: device-side status of the solve, [1]: non-finite input
+  unsigned long long* ctr;     // the sweep counters of the blocked kernels
+};
+// Rules of a batched solve (the handle's configuration).
+struct BatchRule {
+  int cap[2];                  // sweep caps of the FP32 bulk and the FP64 sweeps
+  int stop_permille;           // FP32 -> FP64 hand-over threshold (0 = off)
+  int inner_max32;             // inner sweeps per visit in the FP32 sweeps
+};
+// One launch each; grid z (or one thread) per problem of the batch.
+cudaError_t launch_batch_init(const BatchCol* bc, BatchSweep* bs, int count, int maxm, int maxn, bool mixed,
+                              cudaStream_t s);
+cudaError_t launch_batch_sweep_begin(const BatchCol* bc, BatchSweep* bs, int count, cudaStream_t s);
+cudaError_t launch_batch_sweep_end(const BatchCol* bc, BatchSweep* bs, const BatchRule& rule, int count,
+                                   cudaStream_t s);
+cudaError_t launch_batch_rescale(const BatchCol* bc, BatchSweep* bs, int count, int maxn, cudaStream_t s);
+cudaError_t launch_batch_restart(const BatchCol* bc, BatchSweep* bs, int count, int maxm, int maxn, cudaStream_t s);
+cudaError_t launch_batch_stop(BatchSweep* bs, int count, int status, cudaStream_t s);
+cudaError_t launch_batch_finalize(const BatchCol* bc, BatchSweep* bs, int count, int maxm, int maxn,
+                                  cudaStream_t s);
+
 int blk_vmax(int w, bool cplx);  // real-view width V of the kernels for this w
 cudaError_t launch_gram(const BlkDims& d, const BlkBuffers& b, bool cplx, bool fp32, int step,
-                        cudaStream_t s);
+                        cudaStream_t s, const BlkBatch* bt = nullptr, int nitems = 0, int grid_y = 0);
 cudaError_t launch_inner(const BlkDims& d, const BlkBuffers& b, bool cplx, bool fp32, int step,
-                         const InnerParams& p, cudaStream_t s);
+                         const InnerParams& p, cudaStream_t s, const BlkBatch* bt = nullptr, int nitems = 0);
 cudaError_t launch_apply(const BlkDims& d, const BlkBuffers& b, bool cplx, bool fp32, int step,
-                         cudaStream_t s);
+                         cudaStream_t s, const BlkBatch* bt = nullptr, int nitems = 0, int grid_y = 0);
 // FP64 Gram and apply on the BF16 tensor cores with FP64 accuracy (sliced
 // operands, exact level sums); real-view widths V = 16 and 32
 bool oz_supported(int V);
-cudaError_t launch_gram_oz(const BlkDims& d, const BlkBuffers& b, bool cplx, int step, cudaStream_t s);
-cudaError_t launch_apply_oz(const BlkDims& d, const BlkBuffers& b, bool cplx, int step, cudaStream_t s);
+cudaError_t launch_gram_oz(const BlkDims& d, const BlkBuffers& b, bool cplx, int step, cudaStream_t s,
+                           const BlkBatch* bt = nullptr, int nitems = 0, int grid_y = 0);
+cudaError_t launch_apply_oz(const BlkDims& d, const BlkBuffers& b, bool cplx, int step, cudaStream_t s,
+                            const BlkBatch* bt = nullptr, int nitems = 0, int grid_y = 0);
 
 // -------------------------------------------------- column operations ----
 // prescale: z_j = 1/||g_j||, F <- F Z0, G <- G Z0, Z <- Z0 (FP64, in place)

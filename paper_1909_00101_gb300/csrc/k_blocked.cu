@@ -87,10 +87,13 @@ __host__ __device__ constexpr int gram_threads() {
 }
 
 template <class T, bool CPLX, int V>
-__global__ void __launch_bounds__(gram_threads<T, V>()) k_gram(BlkDims d, BlkBuffers b, int step) {
+__global__ void __launch_bounds__(gram_threads<T, V>()) k_gram(BlkDims d, BlkBuffers b, int step, BlkBatch bt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Ws = reinterpret_cast<T*>(smem_raw);
-  const int slot = blockIdx.x, s = blockIdx.y;
+  int slot;
+  if (!batch_item(bt, blockIdx.x, step, d, b, slot)) return;
+  const int s = blockIdx.y;
+  if (s >= d.rf + d.rg) return;
   PairCols pc;
   if (!load_pair(d, b, step, slot, pc)) return;
   const bool isF = s < d.rf;
@@ -251,7 +254,8 @@ constexpr int INNER_THREADS = 512;  // threads of the pivot kernel
 // Otherwise the sums and Choleskys are FP64 and one warp (two for real
 // pivots) takes all pairs' FP64 parameters, one pair per lane.
 template <class Ti, class To, bool CPLX, int V, bool P32>
-__global__ void __launch_bounds__(INNER_THREADS) k_inner(BlkDims d, BlkBuffers b, int step, InnerParams prm) {
+__global__ void __launch_bounds__(INNER_THREADS) k_inner(BlkDims d, BlkBuffers b, int step, InnerParams prm,
+                                                         BlkBatch bt) {
   constexpr int E = CPLX ? 2 : 1;
   constexpr int NTH = INNER_THREADS;
   constexpr int BMAX = CPLX ? V / 2 : V;  // max columns of the pair
@@ -271,7 +275,8 @@ __global__ void __launch_bounds__(INNER_THREADS) k_inner(BlkDims d, BlkBuffers b
   __shared__ double s_xi[32], s_eta[32];  // chain B of the real parameters
   __shared__ unsigned char s_pair[63][32][2];  // inner round-robin table (M - 1 steps x M / 2 pairs)
 
-  const int slot = blockIdx.x;
+  int slot;
+  if (!batch_item(bt, blockIdx.x, step, d, b, slot, &prm)) return;
   PairCols pc;
   if (!load_pair(d, b, step, slot, pc)) return;
   const int bb = pc.bb;
@@ -859,7 +864,7 @@ size_t inner2_smem() {
 
 template <bool CPLX, int V>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(INNER2_THREADS)
-    k_inner2(BlkDims d, BlkBuffers b, int step, InnerParams prm) {
+    k_inner2(BlkDims d, BlkBuffers b, int step, InnerParams prm, BlkBatch bt) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   constexpr int E = CPLX ? 2 : 1;
@@ -885,9 +890,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(INNER2_THREADS)
   __shared__ unsigned char s_pair[63][32][2];
 
   const int rank = (int)cluster.block_rank();
-  const int slot = blockIdx.x >> 1;
+  int slot;
+  if (!batch_item(bt, blockIdx.x >> 1, step, d, b, slot, &prm)) return;  // the same answer in both CTAs
   PairCols pc;
-  if (!load_pair(d, b, step, slot, pc)) return;  // the same answer in both CTAs
+  if (!load_pair(d, b, step, slot, pc)) return;
   const int bb = pc.bb;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int S = d.rf + d.rg;
@@ -1272,14 +1278,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(INNER2_THREADS)
 
 // --------------------------------------------------------------- apply ----
 template <class T, bool CPLX, int V>
-__global__ void __launch_bounds__(256) k_apply(BlkDims d, BlkBuffers b, int step, int tile0) {
+__global__ void __launch_bounds__(256) k_apply(BlkDims d, BlkBuffers b, int step, int tile0, BlkBatch bt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int slot = blockIdx.x;
+  int slot;
+  if (!batch_item(bt, blockIdx.x, step, d, b, slot)) return;
   PairCols pc;
   if (!load_pair(d, b, step, slot, pc)) return;
   if (!b.flags[slot]) return;
   const int tf = (d.mf + TR - 1) / TR, tg = (d.mg + TR - 1) / TR;
   int tile = tile0 + blockIdx.y;
+  if (tile >= tf + tg + (d.n + TR - 1) / TR) return;
   T* Y;
   long long ld;
   int m;
@@ -1407,26 +1415,34 @@ cudaError_t set_smem(K kern, size_t smem) {
 }
 
 template <class T, bool CPLX, int V>
-cudaError_t gram_v(const BlkDims& d, const BlkBuffers& b, int step, cudaStream_t s) {
+cudaError_t gram_v(const BlkDims& d, const BlkBuffers& b, int step, cudaStream_t s, const BlkBatch* bt, int nitems,
+                   int grid_y) {
   const size_t smem = gram_smem<T, V>();
   auto kern = k_gram<T, CPLX, V>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(d.nslots, d.rf + d.rg);
-  kern<<<grid, gram_threads<T, V>(), smem, s>>>(d, b, step);
+  const BlkBatch one;
+  dim3 grid(bt ? nitems : d.nslots, bt ? grid_y : d.rf + d.rg);
+  kern<<<grid, gram_threads<T, V>(), smem, s>>>(d, b, step, bt ? *bt : one);
   return cudaGetLastError();
 }
 template <class T, bool CPLX, int V>
-cudaError_t apply_v(const BlkDims& d, const BlkBuffers& b, int step, cudaStream_t s) {
+cudaError_t apply_v(const BlkDims& d, const BlkBuffers& b, int step, cudaStream_t s, const BlkBatch* bt, int nitems,
+                    int grid_y) {
   const size_t smem = apply_smem<T, V>();
   auto kern = k_apply<T, CPLX, V>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
+  if (bt) {  // batched: one launch, grid y = the largest problem's row tiles (the planner keeps it <= 65535)
+    kern<<<dim3(nitems, grid_y), 256, smem, s>>>(d, b, step, 0, *bt);
+    return cudaGetLastError();
+  }
+  const BlkBatch one;
   const int tiles = (d.mf + TR - 1) / TR + (d.mg + TR - 1) / TR + (d.n + TR - 1) / TR;
   // tiles of F, G, Z on grid y, in launches of at most 65535 tiles each
   for (int t0 = 0; t0 < tiles; t0 += 65535) {
     dim3 grid(d.nslots, std::min(65535, tiles - t0));
-    kern<<<grid, 256, smem, s>>>(d, b, step, t0);
+    kern<<<grid, 256, smem, s>>>(d, b, step, t0, one);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -1443,14 +1459,17 @@ bool inner_cluster_enabled() {
 }
 
 template <class Ti, class To, bool CPLX, int V>
-cudaError_t inner_v(const BlkDims& d, const BlkBuffers& b, int step, const InnerParams& p, cudaStream_t s) {
+cudaError_t inner_v(const BlkDims& d, const BlkBuffers& b, int step, const InnerParams& p, cudaStream_t s,
+                    const BlkBatch* bt, int nitems) {
+  const BlkBatch one;
+  const int nx = bt ? nitems : d.nslots;
   if constexpr (std::is_same<Ti, double>::value && V <= 32) {
     if (inner_cluster_enabled()) {
       const size_t smem2 = inner2_smem<CPLX, V>();
       auto kern2 = k_inner2<CPLX, V>;
       cudaError_t e2 = set_smem(kern2, smem2);
       if (e2 != cudaSuccess) return e2;
-      kern2<<<2 * d.nslots, INNER2_THREADS, smem2, s>>>(d, b, step, p);
+      kern2<<<2 * nx, INNER2_THREADS, smem2, s>>>(d, b, step, p, bt ? *bt : one);
       return cudaGetLastError();
     }
   }
@@ -1459,7 +1478,7 @@ cudaError_t inner_v(const BlkDims& d, const BlkBuffers& b, int step, const Inner
   auto kern = (can32 && p.par32) ? k_inner<Ti, To, CPLX, V, can32> : k_inner<Ti, To, CPLX, V, false>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  kern<<<d.nslots, INNER_THREADS, smem, s>>>(d, b, step, p);
+  kern<<<nx, INNER_THREADS, smem, s>>>(d, b, step, p, bt ? *bt : one);
   return cudaGetLastError();
 }
 
@@ -1481,38 +1500,40 @@ int blk_vmax(int w, bool cplx) {
     default: return cudaErrorInvalidValue; \
   }
 
-cudaError_t launch_gram(const BlkDims& d, const BlkBuffers& b, bool cplx, bool fp32, int step, cudaStream_t s) {
+cudaError_t launch_gram(const BlkDims& d, const BlkBuffers& b, bool cplx, bool fp32, int step, cudaStream_t s,
+                        const BlkBatch* bt, int nitems, int grid_y) {
   const int V = blk_vmax(d.w, cplx);
   if (cplx) {
-    if (fp32) { HZ_DISPATCH_V(V, (gram_v<float, true, VV>(d, b, step, s))); }
-    else { HZ_DISPATCH_V(V, (gram_v<double, true, VV>(d, b, step, s))); }
+    if (fp32) { HZ_DISPATCH_V(V, (gram_v<float, true, VV>(d, b, step, s, bt, nitems, grid_y))); }
+    else { HZ_DISPATCH_V(V, (gram_v<double, true, VV>(d, b, step, s, bt, nitems, grid_y))); }
   } else {
-    if (fp32) { HZ_DISPATCH_V(V, (gram_v<float, false, VV>(d, b, step, s))); }
-    else { HZ_DISPATCH_V(V, (gram_v<double, false, VV>(d, b, step, s))); }
+    if (fp32) { HZ_DISPATCH_V(V, (gram_v<float, false, VV>(d, b, step, s, bt, nitems, grid_y))); }
+    else { HZ_DISPATCH_V(V, (gram_v<double, false, VV>(d, b, step, s, bt, nitems, grid_y))); }
   }
 }
 
-cudaError_t launch_apply(const BlkDims& d, const BlkBuffers& b, bool cplx, bool fp32, int step, cudaStream_t s) {
+cudaError_t launch_apply(const BlkDims& d, const BlkBuffers& b, bool cplx, bool fp32, int step, cudaStream_t s,
+                         const BlkBatch* bt, int nitems, int grid_y) {
   const int V = blk_vmax(d.w, cplx);
   if (cplx) {
-    if (fp32) { HZ_DISPATCH_V(V, (apply_v<float, true, VV>(d, b, step, s))); }
-    else { HZ_DISPATCH_V(V, (apply_v<double, true, VV>(d, b, step, s))); }
+    if (fp32) { HZ_DISPATCH_V(V, (apply_v<float, true, VV>(d, b, step, s, bt, nitems, grid_y))); }
+    else { HZ_DISPATCH_V(V, (apply_v<double, true, VV>(d, b, step, s, bt, nitems, grid_y))); }
   } else {
-    if (fp32) { HZ_DISPATCH_V(V, (apply_v<float, false, VV>(d, b, step, s))); }
-    else { HZ_DISPATCH_V(V, (apply_v<double, false, VV>(d, b, step, s))); }
+    if (fp32) { HZ_DISPATCH_V(V, (apply_v<float, false, VV>(d, b, step, s, bt, nitems, grid_y))); }
+    else { HZ_DISPATCH_V(V, (apply_v<double, false, VV>(d, b, step, s, bt, nitems, grid_y))); }
   }
 }
 
 
 cudaError_t launch_inner(const BlkDims& d, const BlkBuffers& b, bool cplx, bool fp32, int step,
-                         const InnerParams& p, cudaStream_t s) {
+                         const InnerParams& p, cudaStream_t s, const BlkBatch* bt, int nitems) {
   const int V = blk_vmax(d.w, cplx);
   if (cplx) {
-    if (fp32) { HZ_DISPATCH_V(V, (inner_v<float, float, true, VV>(d, b, step, p, s))); }
-    else { HZ_DISPATCH_V(V, (inner_v<double, double, true, VV>(d, b, step, p, s))); }
+    if (fp32) { HZ_DISPATCH_V(V, (inner_v<float, float, true, VV>(d, b, step, p, s, bt, nitems))); }
+    else { HZ_DISPATCH_V(V, (inner_v<double, double, true, VV>(d, b, step, p, s, bt, nitems))); }
   } else {
-    if (fp32) { HZ_DISPATCH_V(V, (inner_v<float, float, false, VV>(d, b, step, p, s))); }
-    else { HZ_DISPATCH_V(V, (inner_v<double, double, false, VV>(d, b, step, p, s))); }
+    if (fp32) { HZ_DISPATCH_V(V, (inner_v<float, float, false, VV>(d, b, step, p, s, bt, nitems))); }
+    else { HZ_DISPATCH_V(V, (inner_v<double, double, false, VV>(d, b, step, p, s, bt, nitems))); }
   }
 }
 

@@ -11,16 +11,20 @@
 // The arithmetic, per contraction sum_k x_k y_k:
 //   * every x in a set that shares a scale (a column of the Gram slab, a
 //     column of the Y tile, a column of Z-tilde) is written exactly as
-//     x = s 2^e sum_{a=1..7} c_a 2^(-8a) + r, with 2^e above the set's
-//     largest |x|, digits c_a in [0, 255], s the sign of x, |r| < 2^(e-56);
-//     s c_a is an integer that BF16 holds exactly;
+//     x = s 2^e sum_{a=1..8} c_a 2^(-8a) + r, with 2^e above the set's
+//     largest |x|, digits c_a in [0, 255], s the sign of x, |r| < 2^(e-64);
+//     s c_a is an integer that BF16 holds exactly.  Eight digits (64 bits)
+//     keep the full 53-bit significand of every entry within 2^-11 of its
+//     set's largest, so graded data (the rows of a triangular QR factor, a
+//     spread of column norms inside a tile) keep the accuracy of an FP64
+//     product;
 //   * a product of two such expansions is sum_{a,b} 2^(-8(a+b)) (s c_a)(s' c_b);
-//     the terms with a + b <= 8 are kept (the rest weigh below 2^-56 of the
+//     the terms with a + b <= 9 are kept (the rest weigh below 2^-64 of the
 //     scales' product); for each level L = a + b the slice products are summed
-//     by the tensor cores in FP32, exactly, because a level of at most 7
-//     products over at most 32 terms stays below 2^24;
+//     by the tensor cores in FP32, exactly, because a level of at most 8
+//     products over at most 32 terms stays below 2^24 (8 * 32 * 255^2 < 2^24);
 //   * the levels are combined exactly in 128-bit integers,
-//     T = sum_L A_L 2^(8(8-L)), and T 2^(e + e' - 64) is rounded once to the
+//     T = sum_L A_L 2^(8(9-L)), and T 2^(e + e' - 72) is rounded once to the
 //     nearest FP64 value (ties to even).
 // The error of an entry is below about 2^-53 times (number of terms) times
 // the product of the two scales: the size of an FP64 dot product's own error
@@ -43,8 +47,9 @@ namespace hz {
 
 namespace {
 
-constexpr int NSL = 7;  // slices (56 bits)
-constexpr int NLV = 7;  // levels L = 2..8
+constexpr int NSL = 8;  // slices (64 bits)
+constexpr int NLV = 8;  // levels L = 2..9
+constexpr int OZ_EOFF = 72;  // 2^-72: the weight of level L = 2 relative to the two scales
 constexpr int OZ_CHUNK = 32;  // Gram rows per FP32 level sum
 
 __device__ __forceinline__ int exp_field(double x) {
@@ -52,15 +57,15 @@ __device__ __forceinline__ int exp_field(double x) {
   return e ? e : 1;
 }
 
-// The 56-bit fixed-point magnitude X of x relative to the scale whose
-// exponent field is emax (|x| < 2^(emax - 1022), X = |x| 2^(1078 - emax),
+// The 64-bit fixed-point magnitude X of x relative to the scale whose
+// exponent field is emax (|x| < 2^(emax - 1022), X = |x| 2^(1086 - emax),
 // truncated); eadd is added to x's exponent first (x 2^eadd is taken).
-__device__ __forceinline__ unsigned long long fixed56(double x, int emax, int eadd) {
+__device__ __forceinline__ unsigned long long fixed64(double x, int emax, int eadd) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   const int e = (int)((bits >> 52) & 0x7FF);
   const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull);
-  const int sh = (e ? e + eadd : 1 + eadd) - emax + 3;
-  if (sh >= 0) return m << sh;  // sh <= 3: X < 2^56
+  const int sh = (e ? e + eadd : 1 + eadd) - emax + 11;
+  if (sh >= 0) return m << sh;  // sh <= 11: X < 2^64
   return sh > -64 ? (m >> (-sh)) : 0ull;
 }
 
@@ -73,19 +78,20 @@ __device__ __forceinline__ uint32_t bf16_digit(uint32_t c, uint32_t sgn) {
   return (__float_as_uint(f) >> 16) | sgn;
 }
 
-// The seven signed 8-bit digits of x (most significant first) as BF16
+// The eight signed 8-bit digits of x (most significant first) as BF16
 // patterns in the low halves of out[]: x = s 2^e sum_a c_a 2^(-8(a+1)) + r.
-__device__ __forceinline__ void slice7(double x, int emax, int eadd, uint32_t out[NSL]) {
-  const unsigned long long X = fixed56(x, emax, eadd);
+__device__ __forceinline__ void slice8(double x, int emax, int eadd, uint32_t out[NSL]) {
+  const unsigned long long X = fixed64(x, emax, eadd);
   const uint32_t sgn = (uint32_t)((unsigned long long)__double_as_longlong(x) >> 63) << 15;
   const uint32_t h = (uint32_t)(X >> 32), l = (uint32_t)X;
-  out[0] = bf16_digit((h >> 16) & 255u, sgn);
-  out[1] = bf16_digit((h >> 8) & 255u, sgn);
-  out[2] = bf16_digit(h & 255u, sgn);
-  out[3] = bf16_digit(l >> 24, sgn);
-  out[4] = bf16_digit((l >> 16) & 255u, sgn);
-  out[5] = bf16_digit((l >> 8) & 255u, sgn);
-  out[6] = bf16_digit(l & 255u, sgn);
+  out[0] = bf16_digit(h >> 24, sgn);
+  out[1] = bf16_digit((h >> 16) & 255u, sgn);
+  out[2] = bf16_digit((h >> 8) & 255u, sgn);
+  out[3] = bf16_digit(h & 255u, sgn);
+  out[4] = bf16_digit(l >> 24, sgn);
+  out[5] = bf16_digit((l >> 16) & 255u, sgn);
+  out[6] = bf16_digit((l >> 8) & 255u, sgn);
+  out[7] = bf16_digit(l & 255u, sgn);
 }
 
 // An integer-valued FP32 value as a 64-bit integer, with integer operations
@@ -99,13 +105,13 @@ __device__ __forceinline__ long long float_int_to_ll(float f) {
   return (b >> 31) ? -v : v;
 }
 
-// sum_i x_i 2^(8(6 - i)) 2^e2 rounded to the nearest FP64 value (ties to
+// sum_i x_i 2^(8(7 - i)) 2^e2 rounded to the nearest FP64 value (ties to
 // even), with integer operations only.  The sum is formed exactly as
-// H 2^32 + L (H signed 64-bit, L unsigned 32-bit); |x_i| < 2^38 is assumed
-// (level sums over at most OZ_K_MAX rows are below 2^35).
+// H 2^32 + L (H signed 64-bit, L unsigned 32-bit); |x_i| < 2^36 is assumed
+// (level sums over at most OZ_K_MAX rows are below 8 * 2^16 * 255^2 < 2^35).
 __device__ __forceinline__ double levels_to_double(const long long x[NLV], int e2) {
-  const long long hi = (x[0] << 16) + (x[1] << 8) + x[2];
-  const long long lo = (x[3] << 24) + (x[4] << 16) + (x[5] << 8) + x[6];
+  const long long hi = (x[0] << 24) + (x[1] << 16) + (x[2] << 8) + x[3];
+  const long long lo = (x[4] << 24) + (x[5] << 16) + (x[6] << 8) + x[7];
   long long H = hi + (lo >> 32);
   uint32_t L = (uint32_t)lo;
   if (H == 0 && L == 0) return 0.0;
@@ -157,7 +163,7 @@ __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const 
 __device__ __forceinline__ uint32_t ld32(const uint16_t* p) { return *reinterpret_cast<const uint32_t*>(p); }
 
 // level products of one k-step with the A fragments loaded slice by slice
-// (fewer live registers): acc[a + b] += A_a B_b for a + b + 2 <= 8
+// (fewer live registers): acc[a + b] += A_a B_b for a + b + 2 <= 9
 template <class LoadA>
 __device__ __forceinline__ void level_mmas_stream(float acc[NLV][4], LoadA load_a, const uint32_t B[NSL][2]) {
 #pragma unroll
@@ -166,17 +172,17 @@ __device__ __forceinline__ void level_mmas_stream(float acc[NLV][4], LoadA load_
     load_a(a, A);
 #pragma unroll
     for (int b = 0; b < NSL; ++b)
-      if (a + b + 2 <= 8) mma_bf16(acc[a + b], A, B[b]);
+      if (a + b + 2 <= NSL + 1) mma_bf16(acc[a + b], A, B[b]);
   }
 }
 
-// level products of one k-step: acc[L - 2] += A_a B_b for a + b = L <= 8
+// level products of one k-step: acc[L - 2] += A_a B_b for a + b = L <= 9
 __device__ __forceinline__ void level_mmas(float acc[NLV][4], const uint32_t A[NSL][4], const uint32_t B[NSL][2]) {
 #pragma unroll
   for (int a = 0; a < NSL; ++a)
 #pragma unroll
     for (int b = 0; b < NSL; ++b)
-      if (a + b + 2 <= 8) mma_bf16(acc[a + b], A[a], B[b]);
+      if (a + b + 2 <= NSL + 1) mma_bf16(acc[a + b], A[a], B[b]);
 }
 
 // ---------------------------------------------------------------- Gram ----
@@ -201,12 +207,16 @@ __device__ __forceinline__ void oz_gram_tile(int w, int& mt, int& nt) {
 constexpr int GRS = OZ_CHUNK + 8;  // padded row stride of a slice column (bf16)
 
 template <int V, bool CPLX>
-__global__ void __launch_bounds__(32 * oz_gram_warps<V>()) k_gram_oz(BlkDims d, BlkBuffers b, int step) {
+__global__ void __launch_bounds__(32 * oz_gram_warps<V>()) k_gram_oz(BlkDims d, BlkBuffers b, int step,
+                                                                        BlkBatch bt) {
   constexpr int NW = oz_gram_warps<V>();
   constexpr int NT = 32 * NW;
   __shared__ __align__(16) uint16_t Ss[NSL][V][GRS];
   __shared__ int s_emax[V];
-  const int slot = blockIdx.x, s = blockIdx.y;
+  int slot;
+  if (!batch_item(bt, blockIdx.x, step, d, b, slot)) return;
+  const int s = blockIdx.y;
+  if (s >= d.rf + d.rg) return;
   PairCols pc;
   if (!load_pair(d, b, step, slot, pc)) return;
   const bool isF = s < d.rf;
@@ -301,8 +311,8 @@ __global__ void __launch_bounds__(32 * oz_gram_warps<V>()) k_gram_oz(BlkDims d, 
         if constexpr (CPLX) vc = part == 0 ? (c < bb ? c : 2 * c) : (c < bb ? bb + c : 2 * c + 1);
         const int em = s_emax[vc];
         uint32_t s0[NSL], s1[NSL];
-        slice7(pre[u][2 * part], em, 0, s0);
-        slice7(pre[u][2 * part + 1], em, 0, s1);
+        slice8(pre[u][2 * part], em, 0, s0);
+        slice8(pre[u][2 * part + 1], em, 0, s1);
 #pragma unroll
         for (int a = 0; a < NSL; ++a) *reinterpret_cast<uint32_t*>(&Ss[a][vc][rp]) = s0[a] | (s1[a] << 16);
       }
@@ -352,7 +362,7 @@ __global__ void __launch_bounds__(32 * oz_gram_warps<V>()) k_gram_oz(BlkDims d, 
     long long x[NLV];
 #pragma unroll
     for (int L = 0; L < NLV; ++L) x[L] = float_int_to_ll(hi[L][q]) + (long long)__float2int_rn(lo[L][q]);
-    const int e2 = (s_emax[i] - 1022) + (s_emax[j] - 1022) - 64;
+    const int e2 = (s_emax[i] - 1022) + (s_emax[j] - 1022) - OZ_EOFF;
     out[i * V + j] = levels_to_double(x, e2);
   }
 }
@@ -364,7 +374,7 @@ __global__ void __launch_bounds__(32 * oz_gram_warps<V>()) k_gram_oz(BlkDims d, 
 constexpr int ATR = 64;
 
 template <int V, bool CPLX>
-__global__ void __launch_bounds__(256) k_apply_oz(BlkDims d, BlkBuffers b, int step, int tile0) {
+__global__ void __launch_bounds__(256) k_apply_oz(BlkDims d, BlkBuffers b, int step, int tile0, BlkBatch bt) {
   constexpr int YS = V + 8;  // padded row stride of the Y slices (bf16)
   constexpr int TS = V + 8;  // padded stride of a Z slice column (bf16)
   constexpr int NNW = V / 16;  // column tiles (n8) per warp
@@ -374,12 +384,14 @@ __global__ void __launch_bounds__(256) k_apply_oz(BlkDims d, BlkBuffers b, int s
   double* Zd = reinterpret_cast<double*>(Ts + NSL * V * TS);  // [V][V], row k = Z-tilde row
   __shared__ int s_ey[V], s_fz[V];
 
-  const int slot = blockIdx.x;
+  int slot;
+  if (!batch_item(bt, blockIdx.x, step, d, b, slot)) return;
   PairCols pc;
   if (!load_pair(d, b, step, slot, pc)) return;
   if (!b.flags[slot]) return;
   const int tf = (d.mf + ATR - 1) / ATR, tg = (d.mg + ATR - 1) / ATR;
   int tile = tile0 + blockIdx.y;
+  if (tile >= tf + tg + (d.n + ATR - 1) / ATR) return;
   double* Y;
   long long ld;
   int m;
@@ -451,16 +463,16 @@ __global__ void __launch_bounds__(256) k_apply_oz(BlkDims d, BlkBuffers b, int s
   for (int it = threadIdx.x; it < V * (V / 2); it += 256) {
     const int j = it % V, k = 2 * (it / V);
     uint32_t s0[NSL], s1[NSL];
-    slice7(Zd[k * V + j], s_fz[j], s_ey[k] - 1022, s0);
-    slice7(Zd[(k + 1) * V + j], s_fz[j], s_ey[k + 1] - 1022, s1);
+    slice8(Zd[k * V + j], s_fz[j], s_ey[k] - 1022, s0);
+    slice8(Zd[(k + 1) * V + j], s_fz[j], s_ey[k + 1] - 1022, s1);
 #pragma unroll
     for (int a = 0; a < NSL; ++a) *reinterpret_cast<uint32_t*>(&Ts[(a * V + j) * TS + k]) = s0[a] | (s1[a] << 16);
   }
 #pragma unroll
   for (int i = 0; i < NPR; ++i) {
     uint32_t s0[NSL], s1[NSL];
-    slice7(y[i][0], s_ey[yc[i][0]], 0, s0);
-    slice7(y[i][1], s_ey[yc[i][1]], 0, s1);
+    slice8(y[i][0], s_ey[yc[i][0]], 0, s0);
+    slice8(y[i][1], s_ey[yc[i][1]], 0, s1);
     if constexpr (!CPLX) {
 #pragma unroll
       for (int a = 0; a < NSL; ++a)
@@ -522,7 +534,7 @@ __global__ void __launch_bounds__(256) k_apply_oz(BlkDims d, BlkBuffers b, int s
       long long x[NLV];
 #pragma unroll
       for (int L = 0; L < NLV; ++L) x[L] = __float2int_rn(acc[u][L][q]);
-      Ob[j * OS + r] = levels_to_double(x, s_fz[j] - 1022 - 64);
+      Ob[j * OS + r] = levels_to_double(x, s_fz[j] - 1022 - OZ_EOFF);
     }
   __syncthreads();
   if constexpr (!CPLX) {
@@ -566,8 +578,8 @@ __global__ void __launch_bounds__(256) k_slice_kc(int R, int K, const double* __
   for (int k = 2 * lane; k < Kp; k += 64) {
     const double x0 = k < K ? row[k] : 0.0, x1 = k + 1 < K ? row[k + 1] : 0.0;
     uint32_t s0[NSL], s1[NSL];
-    slice7(x0, mx, 0, s0);
-    slice7(x1, mx, 0, s1);
+    slice8(x0, mx, 0, s0);
+    slice8(x1, mx, 0, s1);
 #pragma unroll
     for (int q = 0; q < NSL; ++q) *reinterpret_cast<uint32_t*>(out + q * plane + k) = s0[q] | (s1[q] << 16);
   }
@@ -598,8 +610,8 @@ __global__ void __launch_bounds__(256) k_slice_tr(int R, int K, const double* __
       if (r0 + rr < R && lane < 16) {
         const int kk = 2 * lane;
         uint32_t s0[NSL], s1[NSL];
-        slice7(T[kk][rr], s_e[rr], 0, s0);
-        slice7(T[kk + 1][rr], s_e[rr], 0, s1);
+        slice8(T[kk][rr], s_e[rr], 0, s0);
+        slice8(T[kk + 1][rr], s_e[rr], 0, s1);
         uint16_t* out = S + (size_t)(r0 + rr) * Kp + k0 + kk;
 #pragma unroll
         for (int q = 0; q < NSL; ++q) *reinterpret_cast<uint32_t*>(out + q * plane) = s0[q] | (s1[q] << 16);
@@ -709,7 +721,7 @@ __global__ void __launch_bounds__(256, 2) k_gemm_oz(int M, int N, int K, long lo
     long long x[NLV];
 #pragma unroll
     for (int L = 0; L < NLV; ++L) x[L] = float_int_to_ll(hi[L][q]) + (long long)__float2int_rn(lo[L][q]);
-    const double v = levels_to_double(x, (ea[i] - 1022) + (eb[j] - 1022) - 64);
+    const double v = levels_to_double(x, (ea[i] - 1022) + (eb[j] - 1022) - OZ_EOFF);
     double* cp = C + (size_t)j * ldc + i;
     *cp = beta == 0.0 ? alpha * v : fma(alpha, v, beta * *cp);
   }
@@ -726,18 +738,22 @@ size_t apply_oz_smem() {
 
 bool oz_supported(int V) { return V == 16 || V == 32; }
 
-cudaError_t launch_gram_oz(const BlkDims& d, const BlkBuffers& b, bool cplx, int step, cudaStream_t s) {
+cudaError_t launch_gram_oz(const BlkDims& d, const BlkBuffers& b, bool cplx, int step, cudaStream_t s,
+                           const BlkBatch* bt, int nitems, int grid_y) {
   const int V = blk_vmax(d.w, cplx);
-  // a row split is one exact accumulation: at most OZ_K_MAX rows
+  // a row split is one exact accumulation: at most OZ_K_MAX rows (the batch
+  // planner checks every problem of a batch)
   auto per = [](int m, int nsplit) { return ((m + 63) / 64 + nsplit - 1) / nsplit * 64; };
-  if (per(d.mf, d.rf) > OZ_K_MAX || per(d.mg, d.rg) > OZ_K_MAX) return cudaErrorInvalidValue;
-  dim3 grid(d.nslots, d.rf + d.rg);
+  if (!bt && (per(d.mf, d.rf) > OZ_K_MAX || per(d.mg, d.rg) > OZ_K_MAX)) return cudaErrorInvalidValue;
+  const BlkBatch one;
+  const BlkBatch& bb = bt ? *bt : one;
+  dim3 grid(bt ? nitems : d.nslots, bt ? grid_y : d.rf + d.rg);
   if (V == 16) {
-    if (cplx) k_gram_oz<16, true><<<grid, 32 * oz_gram_warps<16>(), 0, s>>>(d, b, step);
-    else k_gram_oz<16, false><<<grid, 32 * oz_gram_warps<16>(), 0, s>>>(d, b, step);
+    if (cplx) k_gram_oz<16, true><<<grid, 32 * oz_gram_warps<16>(), 0, s>>>(d, b, step, bb);
+    else k_gram_oz<16, false><<<grid, 32 * oz_gram_warps<16>(), 0, s>>>(d, b, step, bb);
   } else if (V == 32) {
-    if (cplx) k_gram_oz<32, true><<<grid, 32 * oz_gram_warps<32>(), 0, s>>>(d, b, step);
-    else k_gram_oz<32, false><<<grid, 32 * oz_gram_warps<32>(), 0, s>>>(d, b, step);
+    if (cplx) k_gram_oz<32, true><<<grid, 32 * oz_gram_warps<32>(), 0, s>>>(d, b, step, bb);
+    else k_gram_oz<32, false><<<grid, 32 * oz_gram_warps<32>(), 0, s>>>(d, b, step, bb);
   } else {
     return cudaErrorInvalidValue;
   }
@@ -745,28 +761,39 @@ cudaError_t launch_gram_oz(const BlkDims& d, const BlkBuffers& b, bool cplx, int
 }
 
 template <int V, bool CPLX>
-static cudaError_t apply_oz_v(const BlkDims& d, const BlkBuffers& b, int step, cudaStream_t s) {
+static cudaError_t apply_oz_v(const BlkDims& d, const BlkBuffers& b, int step, cudaStream_t s, const BlkBatch* bt,
+                              int nitems, int grid_y) {
   const size_t smem = apply_oz_smem<V>();
   auto kern = k_apply_oz<V, CPLX>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
+  if (bt) {  // batched: one launch, grid y = the largest problem's row tiles (the planner keeps it <= 65535)
+    kern<<<dim3(nitems, grid_y), 256, smem, s>>>(d, b, step, 0, *bt);
+    return cudaGetLastError();
+  }
+  const BlkBatch one;
   const int tiles = (d.mf + ATR - 1) / ATR + (d.mg + ATR - 1) / ATR + (d.n + ATR - 1) / ATR;
   // tiles of F, G, Z on grid y, in launches of at most 65535 tiles each
   for (int t0 = 0; t0 < tiles; t0 += 65535) {
     dim3 grid(d.nslots, std::min(65535, tiles - t0));
-    kern<<<grid, 256, smem, s>>>(d, b, step, t0);
+    kern<<<grid, 256, smem, s>>>(d, b, step, t0, one);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
-cudaError_t launch_apply_oz(const BlkDims& d, const BlkBuffers& b, bool cplx, int step, cudaStream_t s) {
+cudaError_t launch_apply_oz(const BlkDims& d, const BlkBuffers& b, bool cplx, int step, cudaStream_t s,
+                            const BlkBatch* bt, int nitems, int grid_y) {
   const int V = blk_vmax(d.w, cplx);
-  if (V == 16) return cplx ? apply_oz_v<16, true>(d, b, step, s) : apply_oz_v<16, false>(d, b, step, s);
-  if (V == 32) return cplx ? apply_oz_v<32, true>(d, b, step, s) : apply_oz_v<32, false>(d, b, step, s);
+  if (V == 16)
+    return cplx ? apply_oz_v<16, true>(d, b, step, s, bt, nitems, grid_y)
+                : apply_oz_v<16, false>(d, b, step, s, bt, nitems, grid_y);
+  if (V == 32)
+    return cplx ? apply_oz_v<32, true>(d, b, step, s, bt, nitems, grid_y)
+                : apply_oz_v<32, false>(d, b, step, s, bt, nitems, grid_y);
   return cudaErrorInvalidValue;
 }
 

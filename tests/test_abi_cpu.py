@@ -125,7 +125,7 @@ def test_workspace_bytes_grows_with_size(lib):
     # QR shortening (real, tall): the n x n sub-problem's workspace plus
     # R_F, R_G, R1_F, R1_G (n^2 each) and a max(m_F, m_G) x n product buffer,
     # plus (fp64_gemm = 1) the BF16 digit planes of the largest product:
-    # 7 digits x 2 bytes for both n x m operands of the Gram F^T F
+    # 8 digits x 2 bytes for both n x m operands of the Gram F^T F
     sh = hz.make_config(path="blocked", shorten=1, fp64_gemm=0)
     n, m = 2048, 4096
     sub = lib.gsvd_workspace_bytes(ctypes.byref(cfg), 0, n, n, n)
@@ -133,19 +133,19 @@ def test_workspace_bytes_grows_with_size(lib):
     assert got >= sub + 8 * (4 * n * n + m * n) and got <= sub + 8 * (4 * n * n + m * n) + 1024
     shoz = hz.make_config(path="blocked", shorten=1, fp64_gemm=1)
     got_oz = lib.gsvd_workspace_bytes(ctypes.byref(shoz), 0, m, m, n)
-    planes = 2 * 7 * 2 * n * m
+    planes = 2 * 8 * 2 * n * m
     assert planes <= got_oz - got <= planes + 65536  # + the per-row scale exponents
     # complex problems are not shortened
     assert lib.gsvd_workspace_bytes(ctypes.byref(sh), 1, m, m, n) == c
     # very tall pairs: the Grams are summed in pieces of at most 65536 rows,
-    # so the planes are those of the m x n x n products (7 digits x 2 bytes
+    # so the planes are those of the m x n x n products (8 digits x 2 bytes
     # of the m x n operand and of the n x n one), not of the m-row Gram
     # (+ one scale exponent per row of both operands)
     n, m = 256, 200000
     base = lib.gsvd_workspace_bytes(ctypes.byref(cfg), 0, n, n, n) + 8 * (4 * n * n + m * n)
     extra = lib.gsvd_workspace_bytes(ctypes.byref(shoz), 0, m, m, n) - base
-    prod = 14 * m * n + 14 * n * n
-    assert prod <= extra <= prod + 4 * (m + n) + 2048 and extra < 2 * 7 * 2 * n * m
+    prod = 16 * m * n + 16 * n * n
+    assert prod <= extra <= prod + 4 * (m + n) + 2048 and extra < 2 * 8 * 2 * n * m
 
 
 def test_size_limits_of_the_header(lib):

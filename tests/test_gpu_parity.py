@@ -385,6 +385,34 @@ def test_batched_blocked_problems_vs_oracle(hz, precision):
         check(p.F, p.G, r, label="batched %s n=%d" % (precision, p.F.shape[1]), case=c)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batched_failures_stay_with_their_problem(hz, precision):
+    """In one batched call the blocked problems advance together; a problem
+    with a non-finite entry (EINVAL, untouched) and one with a zero column of
+    G (ENOTPD) fail alone, and every other problem gets the bits of its
+    single solve (shortening off: the batched path does not shorten)."""
+    shapes = [(150, 130, 96), (200, 150, 120), (90, 80, 70), (130, 140, 100), (300, 260, 128)]
+    pairs = [make_pair(*sh, lo=1e-3, hi=1e3, cond=1e2, seed=700 + k) for k, sh in enumerate(shapes)]
+    F1 = pairs[1].F.copy(order="F")
+    F1[7, 3] = np.nan
+    G3 = pairs[3].G.copy(order="F")
+    G3[:, 11] = 0.0
+    inputs = [(p.F, p.G) for p in pairs]
+    inputs[1] = (F1, pairs[1].G)
+    inputs[3] = (pairs[3].F, G3)
+    with hz.Solver(precision=precision, shorten=0) as s:
+        res = s.solve_batched([(_dev(F), _dev(G)) for F, G in inputs])
+        assert res[1].info["status"] == hz.EINVAL and torch.equal(res[1].U.cpu().isnan().any(), torch.tensor(True))
+        assert res[3].info["status"] == hz.ENOTPD
+        for k in (0, 2, 4):
+            one = s.solve(_dev(inputs[k][0]), _dev(inputs[k][1]))
+            assert res[k].info["status"] == 0 and one.status == 0, (res[k].info, one.info)
+            assert res[k].info["sweeps_fp64"] == one.info["sweeps_fp64"]
+            for a, b in ((res[k].sigma, one.sigma), (res[k].Z, one.Z), (res[k].U, one.U), (res[k].V, one.V)):
+                assert torch.equal(a, b)
+            check(pairs[k].F, pairs[k].G, res[k], label="batched %s n=%d" % (precision, shapes[k][2]))
+
+
 def test_batched_equals_single(hz):
     shapes = [(40, 35, 30), (64, 48, 32), (20, 20, 16), (90, 80, 70), (33, 33, 33)]
     pairs = [make_pair(*s, seed=100 + k) for k, s in enumerate(shapes)]
@@ -483,12 +511,26 @@ def test_status_nonfinite_input(hz):
 
 @pytest.mark.parametrize("path", ["pointwise", "blocked"])
 def test_status_rank_deficient_G(hz, path):
+    """A zero column of G: the prescale (Sec. 2, z_j = 1/||g_j||) has no
+    finite value, the solve reports ENOTPD (and still writes its outputs)."""
     p = make_pair(40, 40, 20, seed=2)
     G = p.G.copy()
     G[:, 5] = 0.0
-    G[:4, 5] = 1.0
-    G[:, 6] = G[:, 5]
     r = hz.solve(_dev(p.F), _dev(G), path=path, block_w=4 if path == "blocked" else 0, shorten=0)
+    assert r.status == hz.ENOTPD
+
+
+def test_status_rank_deficient_G_at_the_first_pivot(hz):
+    """Two equal columns of G meet in the first pivot pair of the row-cyclic
+    order, (0, 1): after the prescale both are (1/2, 1/2, 1/2, 1/2, 0, ...),
+    so b_12 = x = 1 exactly and 1 - x^2 = 0: the 2x2 transformation of
+    Sec. 2.1.2 does not exist and the solve reports ENOTPD."""
+    p = make_pair(40, 40, 20, seed=2)
+    G = p.G.copy()
+    G[:, 0] = 0.0
+    G[:4, 0] = 1.0
+    G[:, 1] = G[:, 0]
+    r = hz.solve(_dev(p.F), _dev(G), path="pointwise", order="row_cyclic")
     assert r.status == hz.ENOTPD
 
 
