@@ -37,6 +37,7 @@
 // column (D^-1), Z-tilde by row (D) and then by column, so every Y column
 // keeps its own relative accuracy.
 #include <cstdint>
+#include <cstdlib>
 #include <type_traits>
 
 #include "blk_pair.cuh"
@@ -109,9 +110,9 @@ __device__ __forceinline__ long long float_int_to_ll(float f) {
 // even), with integer operations only.  The sum is formed exactly as
 // H 2^32 + L (H signed 64-bit, L unsigned 32-bit); |x_i| < 2^36 is assumed
 // (level sums over at most OZ_K_MAX rows are below 8 * 2^16 * 255^2 < 2^35).
-__device__ __forceinline__ double levels_to_double(const long long x[NLV], int e2) {
-  const long long hi = (x[0] << 24) + (x[1] << 16) + (x[2] << 8) + x[3];
-  const long long lo = (x[4] << 24) + (x[5] << 16) + (x[6] << 8) + x[7];
+// (hi 2^32 + lo) 2^e2: the same, from hi = sum_{i<4} x_i 2^(8(3 - i)) and
+// lo = sum_{i>=4} x_i 2^(8(7 - i))
+__device__ __forceinline__ double levels_to_double_hl(long long hi, long long lo, int e2) {
   long long H = hi + (lo >> 32);
   uint32_t L = (uint32_t)lo;
   if (H == 0 && L == 0) return 0.0;
@@ -150,6 +151,12 @@ __device__ __forceinline__ double levels_to_double(const long long x[NLV], int e
   if (ex + 1023 <= 0) return __longlong_as_double((long long)sign);
   if (ex + 1023 >= 2047) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
   return __longlong_as_double((long long)(sign | ((unsigned long long)(ex + 1023) << 52) | (m & 0xFFFFFFFFFFFFFull)));
+}
+
+__device__ __forceinline__ double levels_to_double(const long long x[NLV], int e2) {
+  const long long hi = (x[0] << 24) + (x[1] << 16) + (x[2] << 8) + x[3];
+  const long long lo = (x[4] << 24) + (x[5] << 16) + (x[6] << 8) + x[7];
+  return levels_to_double_hl(hi, lo, e2);
 }
 
 __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2]) {
@@ -734,6 +741,249 @@ size_t apply_oz_smem() {
   return (slices > out ? slices : out) + sizeof(double) * V * V + 16;
 }
 
+// --------------------------------------------- apply on tcgen05 / TMEM ----
+// The block apply [Y_p Y_q] <- [Y_p Y_q] Z-tilde of a tile of 128 rows on the
+// 5th-generation tensor cores: the eight digit planes of the tile (A, 128 x V)
+// and of Z-tilde' (B, V x V) are written to shared memory in the canonical
+// K-major layout of 8 x 8 core matrices; one thread issues the
+// tcgen05.mma.kind::f16 instructions (BF16 operands, FP32 accumulation), one
+// accumulator per level L = a + b (V TMEM columns each, 8 levels); after a
+// tcgen05.commit to an mbarrier every thread reads its row's level sums with
+// tcgen05.ld and recombines them exactly (same arithmetic as k_apply_oz: the
+// level sums are integers below 2^24, so the order of the tensor core's
+// additions does not matter).
+constexpr int TT = 128;  // rows per tile (M of the MMA; TMEM lane = row)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor of tcgen05: start address, leading (K)
+// and stride (M/N) byte offsets of the 8 x 8 core matrices, version 1, no
+// swizzle
+__device__ __forceinline__ uint64_t tc_sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// byte offset of element (r, k) of a K-major operand with K = V: core matrix
+// (r / 8, k / 8) at (r / 8) 16 V + (k / 8) 128, 16 bytes per core-matrix row
+template <int V>
+__device__ __forceinline__ int tc_off(int r, int k) {
+  return (r >> 3) * (16 * V) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&v)[N]);
+template <>
+__device__ __forceinline__ void tmem_ld<8>(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr));
+}
+
+template <int V>
+constexpr size_t apply_tc_smem() {
+  return (size_t)NSL * TT * V * 2 + (size_t)NSL * V * V * 2 + (size_t)V * V * 8 + 1024;
+}
+
+template <int V, bool CPLX>
+__global__ void __launch_bounds__(256, 2) k_apply_tc(BlkDims d, BlkBuffers b, int step, int tile0, BlkBatch bt) {
+  constexpr int H = V / 2;              // real-view columns per thread (two threads per row)
+  constexpr int APL = TT * V * 2;       // bytes of an A digit plane
+  constexpr int BPL = V * V * 2;        // bytes of a B digit plane
+  constexpr uint32_t TCOLS = NSL * V;   // TMEM columns: one V-wide accumulator per level
+  extern __shared__ __align__(128) unsigned char tc_smem[];
+  unsigned char* As = tc_smem;                                   // [NSL][APL]
+  unsigned char* Bs = As + NSL * APL;                            // [NSL][BPL]
+  double* Zd = reinterpret_cast<double*>(Bs + NSL * BPL);        // [V][V], row k = Z-tilde row
+  __shared__ int s_ey[V], s_fz[V];
+  __shared__ uint32_t s_taddr;
+  __shared__ __align__(8) uint64_t s_bar;
+
+  int slot;
+  if (!batch_item(bt, blockIdx.x, step, d, b, slot)) return;
+  PairCols pc;
+  if (!load_pair(d, b, step, slot, pc)) return;
+  if (!b.flags[slot]) return;
+  const int tf = (d.mf + TT - 1) / TT, tg = (d.mg + TT - 1) / TT;
+  int tile = tile0 + blockIdx.y;
+  if (tile >= tf + tg + (d.n + TT - 1) / TT) return;
+  double* Y;
+  long long ld;
+  int m;
+  if (tile < tf) {
+    Y = static_cast<double*>(b.F); ld = b.ldf; m = d.mf;
+  } else if (tile < tf + tg) {
+    tile -= tf; Y = static_cast<double*>(b.G); ld = b.ldg; m = d.mg;
+  } else {
+    tile -= tf + tg; Y = static_cast<double*>(b.Z); ld = b.ldz; m = d.n;
+  }
+  const int r0 = tile * TT;
+  const int bb = pc.bb;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double* zt = static_cast<const double*>(b.ztil) + (size_t)slot * V * V;
+
+  // TMEM for the eight level accumulators (warp 0), the mbarrier of the MMAs
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_taddr)),
+                 "r"(TCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s_bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+
+  // 1. Z-tilde into shared memory; this thread's H real-view values of row
+  //    r = tid % 128: columns h H + [0, H), h = tid / 128 (real view: complex
+  //    column c gives Re in column c and Im in column bb + c; zero beyond 2 bb)
+  for (int idx = tid; idx < V * V; idx += 256) Zd[idx] = zt[idx];
+  if (tid < V) s_ey[tid] = 1;
+  const int r = tid & (TT - 1), h = tid >> 7;
+  const bool live = r0 + r < m;
+  double y[H];
+#pragma unroll
+  for (int c = 0; c < H; ++c) {
+    const int vc = h * H + c;
+    double v = 0.0;
+    if (live) {
+      if constexpr (!CPLX) {
+        if (vc < bb) v = Y[(size_t)pc.gcol(vc) * ld + r0 + r];
+      } else {
+        if (vc < bb) v = Y[2 * ((size_t)pc.gcol(vc) * ld + r0 + r)];
+        else if (vc < 2 * bb) v = Y[2 * ((size_t)pc.gcol(vc - bb) * ld + r0 + r) + 1];
+      }
+    }
+    y[c] = v;
+  }
+  __syncthreads();
+  // 2. column exponents of the tile (four warps share a column: 128 rows)
+#pragma unroll
+  for (int c = 0; c < H; ++c) {
+    const int mx = __reduce_max_sync(FULL, exp_field(y[c]));
+    if (lane == 0) atomicMax(&s_ey[h * H + c], mx);
+  }
+  __syncthreads();
+  // 3. Z' = D Z-tilde (row k scaled by 2^(e_k)): column exponents, then the
+  //    digit planes of B = Z'^T (N = output column j, K = k), eight k per chunk
+  for (int j = warp; j < V; j += 8) {
+    int mx = 1;
+    for (int k = lane; k < V; k += 32) {
+      const double z = Zd[k * V + j];
+      if (z != 0.0) mx = max(mx, exp_field(z) + s_ey[k] - 1022);
+    }
+    mx = __reduce_max_sync(FULL, mx);
+    if (lane == 0) s_fz[j] = mx;
+  }
+  __syncthreads();
+  for (int it = tid; it < V * (V / 2); it += 256) {  // two k per 32-bit word
+    const int j = it / (V / 2), k = 2 * (it % (V / 2));
+    uint32_t d0[NSL], d1[NSL];
+    slice8(Zd[k * V + j], s_fz[j], s_ey[k] - 1022, d0);
+    slice8(Zd[(k + 1) * V + j], s_fz[j], s_ey[k + 1] - 1022, d1);
+#pragma unroll
+    for (int a = 0; a < NSL; ++a) *reinterpret_cast<uint32_t*>(Bs + a * BPL + tc_off<V>(j, k)) = d0[a] | (d1[a] << 16);
+  }
+  // 4. the digit planes of A = the tile (M = row, K = real-view column)
+#pragma unroll
+  for (int c = 0; c < H; c += 2) {
+    uint32_t d0[NSL], d1[NSL];
+    slice8(y[c], s_ey[h * H + c], 0, d0);
+    slice8(y[c + 1], s_ey[h * H + c + 1], 0, d1);
+#pragma unroll
+    for (int a = 0; a < NSL; ++a)
+      *reinterpret_cast<uint32_t*>(As + a * APL + tc_off<V>(r, h * H + c)) = d0[a] | (d1[a] << 16);
+  }
+  // the operands become visible to the tensor core (async proxy)
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t taddr = s_taddr;
+
+  // 5. the level products, issued by one thread: D_L += A_a B_b^T for
+  //    a + b = L, K = V in steps of 16
+  if (tid == 0) {
+    // kind::f16: FP32 accumulator, BF16 A and B, both K-major, N = V, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(V >> 3) << 17) | ((uint32_t)(TT >> 4) << 24);
+#pragma unroll
+    for (int L = 0; L < NLV; ++L) {
+      bool first = true;
+#pragma unroll
+      for (int a = 0; a <= L; ++a) {
+        const int bq = L - a;
+#pragma unroll
+        for (int kk = 0; kk < V / 16; ++kk) {
+          const uint64_t ad = tc_sdesc(smem_u32(As + a * APL) + kk * 256, 128, 16 * V);
+          const uint64_t bd = tc_sdesc(smem_u32(Bs + bq * BPL) + kk * 256, 128, 16 * V);
+          const uint32_t acc = first ? 0u : 1u;
+          asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr + (uint32_t)(L * V)),
+                       "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                       : "memory");
+          first = false;
+        }
+      }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                     smem_u32(&s_bar))
+                 : "memory");
+  }
+  // 6. wait for the products (bounded: on a time-out the tile is left as it
+  //    was and the pass is counted as failed, so the solve reports it)
+  uint32_t done = 0;
+  for (int it = 0; it < (1 << 24) && !done; ++it) {
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done)
+                 : "r"(smem_u32(&s_bar))
+                 : "memory");
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (done) {
+    // 7. this thread's row r = 32 (warp % 4) + lane (its TMEM lane) and
+    //    columns h H + [0, H): the eight level sums of each output, recombined
+    const uint32_t tl = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(h * H);
+#pragma unroll 1
+    for (int cg = 0; cg < H; cg += 8) {  // eight outputs at a time
+      long long hi[8], lo[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) hi[c] = lo[c] = 0;
+#pragma unroll
+      for (int L = 0; L < NLV; ++L) {
+        uint32_t v[8];
+        tmem_ld<8>(tl + (uint32_t)(L * V + cg), v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        const int sh = 24 - 8 * (L & 3);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const long long x = float_int_to_ll(__uint_as_float(v[c])) << sh;
+          if (L < 4) hi[c] += x; else lo[c] += x;
+        }
+      }
+      if (live) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int j = h * H + cg + c;
+          if (j >= (CPLX ? 2 : 1) * bb) continue;
+          const double out = levels_to_double_hl(hi[c], lo[c], s_fz[j] - 1022 - OZ_EOFF);
+          if constexpr (!CPLX) {
+            Y[(size_t)pc.gcol(j) * ld + r0 + r] = out;
+          } else {
+            if (j < bb) Y[2 * ((size_t)pc.gcol(j) * ld + r0 + r)] = out;
+            else Y[2 * ((size_t)pc.gcol(j - bb) * ld + r0 + r) + 1] = out;
+          }
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicAdd(&b.ctr[2], 1ull);  // reported as a failed pass (the solve returns ENOTPD)
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(TCOLS) : "memory");
+}
+
 }  // namespace
 
 bool oz_supported(int V) { return V == 16 || V == 32; }
@@ -785,9 +1035,47 @@ static cudaError_t apply_oz_v(const BlkDims& d, const BlkBuffers& b, int step, c
   return cudaSuccess;
 }
 
+// the apply on tcgen05 (GSVD_APPLY_TC=0 selects the mma.sync kernel, for comparisons)
+static bool apply_tc_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("GSVD_APPLY_TC");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+template <int V, bool CPLX>
+static cudaError_t apply_tc_v(const BlkDims& d, const BlkBuffers& b, int step, cudaStream_t s, const BlkBatch* bt,
+                              int nitems, int grid_y) {
+  constexpr size_t smem = apply_tc_smem<V>();
+  auto kern = k_apply_tc<V, CPLX>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (bt) {  // batched: grid y sized for 64-row tiles; the extra blocks leave at once
+    kern<<<dim3(nitems, grid_y), 256, smem, s>>>(d, b, step, 0, *bt);
+    return cudaGetLastError();
+  }
+  const BlkBatch one;
+  const int tiles = (d.mf + TT - 1) / TT + (d.mg + TT - 1) / TT + (d.n + TT - 1) / TT;
+  for (int t0 = 0; t0 < tiles; t0 += 65535) {
+    kern<<<dim3(d.nslots, std::min(65535, tiles - t0)), 256, smem, s>>>(d, b, step, t0, one);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_apply_oz(const BlkDims& d, const BlkBuffers& b, bool cplx, int step, cudaStream_t s,
                             const BlkBatch* bt, int nitems, int grid_y) {
   const int V = blk_vmax(d.w, cplx);
+  if (apply_tc_enabled()) {
+    if (V == 16)
+      return cplx ? apply_tc_v<16, true>(d, b, step, s, bt, nitems, grid_y)
+                  : apply_tc_v<16, false>(d, b, step, s, bt, nitems, grid_y);
+    if (V == 32)
+      return cplx ? apply_tc_v<32, true>(d, b, step, s, bt, nitems, grid_y)
+                  : apply_tc_v<32, false>(d, b, step, s, bt, nitems, grid_y);
+  }
   if (V == 16)
     return cplx ? apply_oz_v<16, true>(d, b, step, s, bt, nitems, grid_y)
                 : apply_oz_v<16, false>(d, b, step, s, bt, nitems, grid_y);
