@@ -98,9 +98,11 @@ typedef struct {
                                Gram sums, the two Choleskys, the 2x2 parameters) in FP32, whose inputs
                                are FP32 dot products anyway (default); 0 = those in FP64 */
   int32_t fp64_gemm;        /* blocked FP64 sweeps: pivot Grams and block applies 1 = on the BF16 tensor
-                               cores with FP64 accuracy (operands split into 8-bit integer slices,
-                               exact level sums, one rounding; default, block widths with 2w <= 32
-                               real / 4w <= 32 complex), 0 = FP64 DMMA */
+                               cores with FP64 accuracy (operands split into eight 8-bit integer
+                               slices, exact level sums, one rounding; mma.sync; default, block widths
+                               with 2w <= 32 real / 4w <= 32 complex), 2 = the same with the block
+                               apply issued as tcgen05.mma with its level sums in tensor memory,
+                               0 = FP64 DMMA */
   int32_t fp32_stop_permille; /* mixed precision: the FP32 bulk sweeps stop (and the FP64 sweeps take
                                over) after a sweep in which big transformations number fewer than
                                this many per mille of the pivot pairs examined (default 50); 0 = run

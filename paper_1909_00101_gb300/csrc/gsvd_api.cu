@@ -202,7 +202,6 @@ bool make_plan(const gsvd_config& cfg, int dtype, int64_t mf, int64_t mg, int64_
     P.total = P.off_status + 256;
     return true;
   }
-  if (cfg.variant != 0) return false;  // variants 1-3: pointwise kernel only
   P.path = GSVD_PATH_BLOCKED;
   P.w = choose_w(cfg, P.cplx, (int)n);
   P.V = blk_vmax(P.w, P.cplx);
@@ -214,6 +213,8 @@ bool make_plan(const gsvd_config& cfg, int dtype, int64_t mf, int64_t mg, int64_
     P.V = blk_vmax(P.w, P.cplx);
     P.nblk = (int)((n + P.w - 1) / P.w);
   }
+  // variants 1-3 (Sec. 2.6) run in the FP64 pivot step of the two-CTA kernel
+  if (cfg.variant != 0 && !inner_variants_supported(P.V)) return false;
   P.neff = P.nblk + (P.nblk & 1);
   P.nslots = P.neff / 2;
   P.steps = P.neff - 1;
@@ -421,7 +422,8 @@ int run_sweeps(const Plan& P, const gsvd_config& cfg, bool fp32, void* F, long l
   d.mf = P.mf; d.mg = P.mg; d.n = P.n; d.w = P.w; d.nblk = P.nblk; d.nslots = P.nslots;
   // FP64 sweeps: Gram and apply on the tensor cores (sliced operands) or on
   // the FP64 pipe (DMMA)
-  const bool oz = !fp32 && cfg.fp64_gemm == 1 && oz_supported(P.V);
+  const bool oz = !fp32 && cfg.fp64_gemm >= 1 && oz_supported(P.V);
+  const bool tc = cfg.fp64_gemm == 2;  // the apply on tcgen05
   d.rf = (fp32 || oz) ? P.rf32 : P.rf;
   d.rg = (fp32 || oz) ? P.rg32 : P.rg;
   d.trows = 64;
@@ -445,6 +447,8 @@ int run_sweeps(const Plan& P, const gsvd_config& cfg, bool fp32, void* F, long l
   ip.crit2 = cfg.criterion == 2;
   ip.chol_skip = fp32;
   ip.par32 = fp32 && cfg.fp32_params != 0;
+  ip.enhanced = !fp32 && (cfg.variant & 1) != 0;  // the variants act in the FP64 sweeps
+  ip.dscale = !fp32 && (cfg.variant & 2) != 0;
   int sw = 0;
   bool converged = false;
   const bool prof = cfg.profile != 0;
@@ -460,7 +464,7 @@ int run_sweeps(const Plan& P, const gsvd_config& cfg, bool fp32, void* F, long l
       if (prof) { kt.mark(kb + 0, s); kt.mark(kb + 1, s); }
       CK(launch_inner(d, b, P.cplx, fp32, k, ip, s));
       if (prof) { kt.mark(kb + 1, s); kt.mark(kb + 2, s); }
-      CK(oz ? launch_apply_oz(d, b, P.cplx, k, s) : launch_apply(d, b, P.cplx, fp32, k, s));
+      CK(oz ? launch_apply_oz(d, b, P.cplx, k, s, tc) : launch_apply(d, b, P.cplx, fp32, k, s));
       if (prof) kt.mark(kb + 2, s);
     }
     CK(cudaMemcpyAsync(h_ctr, b.ctr, NCTR * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
@@ -524,6 +528,8 @@ int solve_pointwise(const gsvd_config& cfg, const gsvd_problem* ps, const int* i
     slots = std::max(slots, rowcyc ? std::max(1, n / 2) : std::max(1, (n + (n & 1)) / 2));
   }
   const size_t pb = align256(sizeof(PwProblem) * count);
+  SolveEvents ev;  // the launch's time is every problem's (they run together)
+  cudaEventRecord(ev.e0, s);
   DevBuf tmp;
   CK(tmp.ensure(2 * pb + sizeof(PwStats) * count, s));
   unsigned char* base = static_cast<unsigned char*>(tmp.p);
@@ -562,10 +568,14 @@ int solve_pointwise(const gsvd_config& cfg, const gsvd_problem* ps, const int* i
     CK(launch_pointwise(d_probs, (int)sub.size(), slots, kind == 1, false, smem, prm, s));
   }
   std::vector<PwStats> hs(count);
+  cudaEventRecord(ev.e1, s);
   CK(cudaMemcpyAsync(hs.data(), d_stats, sizeof(PwStats) * count, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ev.e0, ev.e1);
   for (int k = 0; k < count; ++k) {
     gsvd_info& in = infos[idx[k]];
+    in.t_total_us = ms * 1e3;
     in.status = hs[k].status;
     in.sweeps_fp64 = hs[k].sweeps;
     in.sweeps_fp32 = 0;
@@ -595,7 +605,7 @@ size_t shortened_offset(const gsvd_config& cfg, int64_t n) {
 // the Grams F^T F (n x n over one piece of at most OZ_K_MAX of the m rows)
 // and the products m x n x n
 size_t shortened_oz_bytes(const gsvd_config& cfg, int64_t mf, int64_t mg, int64_t n) {
-  if (cfg.fp64_gemm != 1) return 0;
+  if (cfg.fp64_gemm == 0) return 0;
   const int m = (int)std::max(mf, mg);
   return std::max(dgemm_oz_ws_bytes((int)n, (int)n, std::min(m, OZ_K_MAX)), dgemm_oz_ws_bytes(m, (int)n, (int)n));
 }
@@ -990,7 +1000,7 @@ int solve_blocked_batch(gsvd_ctx* h, const gsvd_problem* ps, const std::vector<i
     g.cplx = kv.first.first != 0;
     g.V = kv.first.second;
     g.w = plans[kv.second[0]].w;
-    g.oz = h->cfg.fp64_gemm == 1 && oz_supported(g.V);
+    g.oz = h->cfg.fp64_gemm >= 1 && oz_supported(g.V);
     g.item0 = (int)items.size();
     for (int k : kv.second) {
       const Plan& Pk = plans[k];
@@ -1032,13 +1042,12 @@ int solve_blocked_batch(gsvd_ctx* h, const gsvd_problem* ps, const std::vector<i
     const Plan& Pk = plans[k];
     const gsvd_config& c = cfgs[k];
     unsigned char* w = wbase + woff[k];
-    BlkProb bp;
-    std::memset(&bp, 0, sizeof bp);
+    BlkProb bp{};
     for (int ph = 0; ph < 2; ++ph) {
       const bool fp32 = ph == 0;
       BlkDims& d = bp.d[ph];
       d.mf = Pk.mf; d.mg = Pk.mg; d.n = Pk.n; d.w = Pk.w; d.nblk = Pk.nblk; d.nslots = Pk.nslots;
-      const bool oz = !fp32 && c.fp64_gemm == 1 && oz_supported(Pk.V);
+      const bool oz = !fp32 && c.fp64_gemm >= 1 && oz_supported(Pk.V);
       d.rf = (fp32 || oz) ? Pk.rf32 : Pk.rf;
       d.rg = (fp32 || oz) ? Pk.rg32 : Pk.rg;
       d.trows = 64;
@@ -1064,6 +1073,8 @@ int solve_blocked_batch(gsvd_ctx* h, const gsvd_problem* ps, const std::vector<i
       ip.crit2 = c.criterion == 2;
       ip.chol_skip = fp32;
       ip.par32 = fp32 && c.fp32_params != 0;
+      ip.enhanced = !fp32 && (c.variant & 1) != 0;
+      ip.dscale = !fp32 && (c.variant & 2) != 0;
     }
     bp.steps = Pk.steps;
     bp.tiles = (Pk.mf + 63) / 64 + (Pk.mg + 63) / 64 + (Pk.n + 63) / 64;
@@ -1132,7 +1143,7 @@ int solve_blocked_batch(gsvd_ctx* h, const gsvd_problem* ps, const std::vector<i
                  : launch_gram(dd, bb, g.cplx, fp32, k, s, &bt, g.nitems, g.gy_gram[ph]);
           if (e == cudaSuccess) e = launch_inner(dd, bb, g.cplx, fp32, k, g.ip[ph], s, &bt, g.nitems);
           if (e == cudaSuccess)
-            e = oz ? launch_apply_oz(dd, bb, g.cplx, k, s, &bt, g.nitems, g.gy_apply)
+            e = oz ? launch_apply_oz(dd, bb, g.cplx, k, s, h->cfg.fp64_gemm == 2, &bt, g.nitems, g.gy_apply)
                    : launch_apply(dd, bb, g.cplx, fp32, k, s, &bt, g.nitems, g.gy_apply);
         }
       }
@@ -1317,6 +1328,7 @@ int gsvd_create(gsvd_handle* h, const gsvd_config* cfg, void* stream) {
     gsvd_config_default(&c->cfg);
   if (c->cfg.max_sweeps < 1 || c->cfg.inner_max_sweeps < 1 || c->cfg.fp32_max_sweeps < 0 || c->cfg.timeout_ms < 0 ||
       (c->cfg.criterion != 1 && c->cfg.criterion != 2) || c->cfg.max_inflight < 1 ||
+      c->cfg.fp64_gemm < 0 || c->cfg.fp64_gemm > 2 ||
       c->cfg.variant < 0 || c->cfg.variant > 3 ||
       (c->cfg.precision != GSVD_PREC_FP64 && c->cfg.precision != GSVD_PREC_MIXED)) {
     delete c;

@@ -272,6 +272,22 @@ __device__ __forceinline__ PivotOutT<T> pivot_real(T a11, T a22, T a12, T x, T t
   return real_combine(a11, a22, a12, x, r, xi, eta, sort, f32cls, crit2);
 }
 
+// App. A: c = RD(a b), d = a b - c >= 0 (exact, one fma); the enhanced dot
+// product is the sum of the c plus the sum of the d
+__device__ __forceinline__ void enh_acc(double& c, double& d, double a, double b) {
+  const double p = __dmul_rd(a, b);
+  c += p;
+  d += fma(a, b, -p);
+}
+
+// App. A, the simpler procedure for ||a||^2 of complex data: one element's
+// term (e + the smaller c) + the larger c, e = d_re + d_im
+__device__ __forceinline__ double enh_abs2(double re, double im) {
+  const double cr = __dmul_rd(re, re), ci = __dmul_rd(im, im);
+  const double e = fma(re, re, -cr) + fma(im, im, -ci);
+  return cr <= ci ? (e + cr) + ci : (e + ci) + cr;
+}
+
 // Named barrier for the two parameter warps (barrier 1, 64 threads).
 __device__ __forceinline__ void param_pair_barrier() { asm volatile("bar.sync 1, 64;\n" ::: "memory"); }
 

@@ -86,6 +86,8 @@ struct InnerParams {
   bool crit2;
   bool chol_skip;      // Cholesky failure: skip the visit (FP32 bulk) instead of failing
   bool par32;          // FP32 bulk sweeps: 2x2 parameters in FP32 (else FP64)
+  bool enhanced = false;  // FP64 sweeps, variants +1: the enhanced dot products of App. A
+  bool dscale = false;    // FP64 sweeps, variants +2: no inner prescale, each pivot pair rescaled by D-hat
 };
 
 // Batched sweeps (gsvd_solve_batched): many blocked problems advance one
@@ -160,6 +162,8 @@ cudaError_t launch_batch_finalize(const BatchCol* bc, BatchSweep* bs, int count,
                                   cudaStream_t s);
 
 int blk_vmax(int w, bool cplx);  // real-view width V of the kernels for this w
+// the variants of Sec. 2.6 run in the FP64 pivot step of width V (the two-CTA kernel)
+bool inner_variants_supported(int V);
 cudaError_t launch_gram(const BlkDims& d, const BlkBuffers& b, bool cplx, bool fp32, int step,
                         cudaStream_t s, const BlkBatch* bt = nullptr, int nitems = 0, int grid_y = 0);
 cudaError_t launch_inner(const BlkDims& d, const BlkBuffers& b, bool cplx, bool fp32, int step,
@@ -171,7 +175,8 @@ cudaError_t launch_apply(const BlkDims& d, const BlkBuffers& b, bool cplx, bool 
 bool oz_supported(int V);
 cudaError_t launch_gram_oz(const BlkDims& d, const BlkBuffers& b, bool cplx, int step, cudaStream_t s,
                            const BlkBatch* bt = nullptr, int nitems = 0, int grid_y = 0);
-cudaError_t launch_apply_oz(const BlkDims& d, const BlkBuffers& b, bool cplx, int step, cudaStream_t s,
+// tc: issue the level products as tcgen05.mma with TMEM accumulators (else mma.sync)
+cudaError_t launch_apply_oz(const BlkDims& d, const BlkBuffers& b, bool cplx, int step, cudaStream_t s, bool tc,
                             const BlkBatch* bt = nullptr, int nitems = 0, int grid_y = 0);
 
 // -------------------------------------------------- column operations ----

@@ -857,7 +857,7 @@ size_t inner2_smem() {
   constexpr int BMAX = CPLX ? V / 2 : V;
   constexpr int RH = (BMAX + 1) / 2;
   constexpr int NPMAX = BMAX / 2;
-  return sizeof(double) * (2 * E * BMAX * BMAX + 3 * E * RH * BMAX + 2 * NPMAX * 8 + 2 * BMAX) +
+  return sizeof(double) * (2 * E * BMAX * BMAX + 3 * E * RH * BMAX + 2 * NPMAX * 16 + 2 * BMAX + 64) +
          sizeof(PivInT<double>) * (NPMAX + 1) + sizeof(PivZ<double>) * (NPMAX + 1) +
          sizeof(uint16_t) * (BMAX * (BMAX + 1) / 2) + 16;
 }
@@ -877,10 +877,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(INNER2_THREADS)
   double* Fl = Bm + E * BMAX * BMAX;                // own rows: E RH x BMAX, column-major
   double* Gl = Fl + E * RH * BMAX;
   double* Zl = Gl + E * RH * BMAX;
-  double* part = Zl + E * RH * BMAX;                // [2][NPMAX][8] partial dot products
-  double* nrm = part + 2 * NPMAX * 8;               // [BMAX] partial column norms
+  double* part = Zl + E * RH * BMAX;                // [2][NPMAX][16] partial dot products
+  double* nrm = part + 2 * NPMAX * 16;              // [BMAX] partial column norms
   double* th = nrm + BMAX;                          // [BMAX] prescale z_j, then theta_j
-  PivInT<double>* pin = reinterpret_cast<PivInT<double>*>(th + BMAX);
+  double* s_d = th + BMAX;                          // [2][32] D-hat of each pair of a step
+  PivInT<double>* pin = reinterpret_cast<PivInT<double>*>(s_d + 64);
   PivZ<double>* pout = reinterpret_cast<PivZ<double>*>(pin + NPMAX + 1);
   uint16_t* s_tri = reinterpret_cast<uint16_t*>(pout + NPMAX + 1);
   __shared__ int s_ctr[4];  // all, big, fail, any-change
@@ -1006,7 +1007,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(INNER2_THREADS)
       sq = fma(v, v, sq);
     }
     sq = warp_sum(sq);
-    if (lane == 0) th[j] = 1.0 / sqrt(sq);
+    if (lane == 0) th[j] = prm.dscale ? 1.0 : 1.0 / sqrt(sq);  // D-hat variants: no inner prescale
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < ldl * bb; idx += blockDim.x) {
@@ -1045,35 +1046,75 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(INNER2_THREADS)
           j = s_pair[st][k][1];
           valid = j < bb;
         }
+        // slots of a pair: [0, 4) a11, a22, a12 (complex: Re, Im), real x;
+        // [4, 8) the App. A error parts of those (real, enhanced) or Re, Im
+        // of b12 (complex); [8, 12) b11, b22 (D-hat) and their error parts
         double v[4] = {0.0, 0.0, 0.0, 0.0};
         double w[4] = {0.0, 0.0, 0.0, 0.0};
+        double u[4] = {0.0, 0.0, 0.0, 0.0};
         if (valid && hl < nr) {
           if constexpr (!CPLX) {
             const double fi = Fl[i * ldl + hl], fj = Fl[j * ldl + hl];
-            v[0] = fi * fi;
-            v[1] = fj * fj;
-            v[2] = fi * fj;
-            v[3] = Gl[i * ldl + hl] * Gl[j * ldl + hl];
+            const double gi = Gl[i * ldl + hl], gj = Gl[j * ldl + hl];
+            if (prm.enhanced) {  // App. A: RD(a b) and the exact remainder a b - RD(a b), summed apart
+              const double p[4] = {fi, fj, fi, gi}, r[4] = {fi, fj, fj, gj};
+#pragma unroll
+              for (int t = 0; t < 4; ++t) {
+                v[t] = __dmul_rd(p[t], r[t]);
+                w[t] = fma(p[t], r[t], -v[t]);
+              }
+              if (prm.dscale) {
+                u[0] = __dmul_rd(gi, gi);
+                u[1] = __dmul_rd(gj, gj);
+                u[2] = fma(gi, gi, -u[0]);
+                u[3] = fma(gj, gj, -u[1]);
+              }
+            } else {
+              v[0] = fi * fi;
+              v[1] = fj * fj;
+              v[2] = fi * fj;
+              v[3] = gi * gj;
+              if (prm.dscale) {
+                u[0] = gi * gi;
+                u[1] = gj * gj;
+              }
+            }
           } else {
             const double fir = Fl[i * ldl + 2 * hl], fii = Fl[i * ldl + 2 * hl + 1];
             const double fjr = Fl[j * ldl + 2 * hl], fji = Fl[j * ldl + 2 * hl + 1];
             const double gir = Gl[i * ldl + 2 * hl], gii = Gl[i * ldl + 2 * hl + 1];
             const double gjr = Gl[j * ldl + 2 * hl], gji = Gl[j * ldl + 2 * hl + 1];
-            v[0] = fma(fir, fir, fii * fii);
-            v[1] = fma(fjr, fjr, fji * fji);
+            if (prm.enhanced) {  // the norms by App. A's simpler procedure; off-diagonals ordinary
+              v[0] = enh_abs2(fir, fii);
+              v[1] = enh_abs2(fjr, fji);
+              if (prm.dscale) {
+                u[0] = enh_abs2(gir, gii);
+                u[1] = enh_abs2(gjr, gji);
+              }
+            } else {
+              v[0] = fma(fir, fir, fii * fii);
+              v[1] = fma(fjr, fjr, fji * fji);
+              if (prm.dscale) {
+                u[0] = fma(gir, gir, gii * gii);
+                u[1] = fma(gjr, gjr, gji * gji);
+              }
+            }
             v[2] = fma(fir, fjr, fii * fji);   // Re(conj(f_i) f_j)
             v[3] = fma(fir, fji, -fii * fjr);  // Im(conj(f_i) f_j)
             w[0] = fma(gir, gjr, gii * gji);
             w[1] = fma(gir, gji, -gii * gjr);
           }
         }
+        const bool need_w = CPLX || prm.enhanced;
         const double sv = half_sum4(v);
-        double swv = 0.0;
-        if constexpr (CPLX) swv = half_sum4(w);
+        const double swv = need_w ? half_sum4(w) : 0.0;
+        const double suv = prm.dscale ? half_sum4(u) : 0.0;
         const int q = ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
         if (valid && (lane & 3) == 0) {
-          part[(buf * NPMAX + k) * 8 + q] = sv;
-          if constexpr (CPLX) part[(buf * NPMAX + k) * 8 + 4 + q] = swv;
+          double* pp = part + (buf * NPMAX + k) * 16;
+          pp[q] = sv;
+          if (need_w) pp[4 + q] = swv;
+          if (prm.dscale) pp[8 + q] = suv;
         }
       }
       // b. the two halves of every dot product meet
@@ -1085,14 +1126,48 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(INNER2_THREADS)
         for (int t = threadIdx.x; t < npairs * NV; t += blockDim.x) {
           const int k = t / NV, qq = t % NV;
           if (s_pair[st][k][1] >= bb) continue;
-          const int off = (buf * NPMAX + k) * 8 + qq;
-          const double tot = part[off] + peer[off];  // a + b = b + a: the same bits in both CTAs
+          const int off = (buf * NPMAX + k) * 16 + qq;
+          double tot = part[off] + peer[off];  // a + b = b + a: the same bits in both CTAs
+          if (!CPLX && prm.enhanced) tot = tot + (part[off + 4] + peer[off + 4]);
           double* pk = reinterpret_cast<double*>(&pin[k]);  // a11, a22, ar, ai, br, bi
           if constexpr (!CPLX) {
             if (qq < 3) pk[qq] = tot;
             else { pk[4] = tot; pk[3] = 0.0; pk[5] = 0.0; }
           } else {
             pk[qq] = tot;
+          }
+        }
+        if (prm.dscale) {
+          // D-hat variants (Sec. 2.1): A' = D A D, B' = D B D with
+          // D_kk = 1/sqrt(b_kk) where b_kk != 1 (as the pointwise kernel)
+          __syncthreads();
+          for (int k = threadIdx.x; k < npairs; k += blockDim.x) {
+            if (s_pair[st][k][1] >= bb) continue;
+            const int off = (buf * NPMAX + k) * 16 + 8;
+            double bii = part[off] + peer[off], bjj = part[off + 1] + peer[off + 1];
+            if (!CPLX && prm.enhanced) {
+              bii = bii + (part[off + 2] + peer[off + 2]);
+              bjj = bjj + (part[off + 3] + peer[off + 3]);
+            }
+            PivInT<double> pv = pin[k];
+            double d1 = 1.0, d2 = 1.0;
+            if (bii != 1.0 && bii > 0.0) {
+              pv.a11 = pv.a11 / bii;
+              d1 = 1.0 / sqrt(bii);
+              pv.ar *= d1; pv.ai *= d1; pv.br *= d1; pv.bi *= d1;
+            }
+            if (bjj != 1.0 && bjj > 0.0) {
+              pv.a22 = pv.a22 / bjj;
+              d2 = 1.0 / sqrt(bjj);
+              pv.ar *= d2; pv.ai *= d2; pv.br *= d2; pv.bi *= d2;
+            }
+            if (!(bii > 0.0) || !(bjj > 0.0)) {  // a zero column of G-hat: b12 = 1 makes the pivot fail (ENOTPD)
+              pv.br = 1.0;
+              pv.bi = 0.0;
+            }
+            pin[k] = pv;
+            s_d[k] = d1;
+            s_d[32 + k] = d2;
           }
         }
       }
@@ -1143,6 +1218,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(INNER2_THREADS)
         }
         if (warp == 0) {
           if (have) {
+            if (prm.dscale && (o.flags & PV_ROT)) {  // Z-hat = D Z-hat': rows times D11, D22
+              const double d1 = s_d[lane], d2 = s_d[32 + lane];
+              o.z11 *= d1; o.z12 *= d1; o.z12i *= d1;
+              o.z21 *= d2; o.z21i *= d2; o.z22 *= d2;
+            }
             PivZ<double> zq;
             zq.z11 = o.z11; zq.z12 = o.z12; zq.z21 = o.z21; zq.z22 = o.z22;
             zq.z12i = CPLX ? o.z12i : 0.0;
@@ -1483,6 +1563,8 @@ cudaError_t inner_v(const BlkDims& d, const BlkBuffers& b, int step, const Inner
 }
 
 }  // namespace
+
+bool inner_variants_supported(int V) { return V <= 32 && inner_cluster_enabled(); }
 
 int blk_vmax(int w, bool cplx) {
   const int v = cplx ? 4 * w : 2 * w;

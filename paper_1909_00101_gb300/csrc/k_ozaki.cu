@@ -1035,15 +1035,6 @@ static cudaError_t apply_oz_v(const BlkDims& d, const BlkBuffers& b, int step, c
   return cudaSuccess;
 }
 
-// the apply on tcgen05 (GSVD_APPLY_TC=0 selects the mma.sync kernel, for comparisons)
-static bool apply_tc_enabled() {
-  static const bool on = [] {
-    const char* e = std::getenv("GSVD_APPLY_TC");
-    return !(e && e[0] == '0');
-  }();
-  return on;
-}
-
 template <int V, bool CPLX>
 static cudaError_t apply_tc_v(const BlkDims& d, const BlkBuffers& b, int step, cudaStream_t s, const BlkBatch* bt,
                               int nitems, int grid_y) {
@@ -1065,10 +1056,10 @@ static cudaError_t apply_tc_v(const BlkDims& d, const BlkBuffers& b, int step, c
   return cudaSuccess;
 }
 
-cudaError_t launch_apply_oz(const BlkDims& d, const BlkBuffers& b, bool cplx, int step, cudaStream_t s,
+cudaError_t launch_apply_oz(const BlkDims& d, const BlkBuffers& b, bool cplx, int step, cudaStream_t s, bool tc,
                             const BlkBatch* bt, int nitems, int grid_y) {
   const int V = blk_vmax(d.w, cplx);
-  if (apply_tc_enabled()) {
+  if (tc) {
     if (V == 16)
       return cplx ? apply_tc_v<16, true>(d, b, step, s, bt, nitems, grid_y)
                   : apply_tc_v<16, false>(d, b, step, s, bt, nitems, grid_y);

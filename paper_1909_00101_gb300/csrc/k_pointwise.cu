@@ -54,22 +54,6 @@ __device__ __forceinline__ bool pw_pair(bool rowcyc, int n, int st, int k, int& 
   return j < n;
 }
 
-// App. A: c = RD(a b), d = a b - c >= 0 (exact, one fma); the enhanced dot
-// product is the sum of the c plus the sum of the d
-__device__ __forceinline__ void enh_acc(double& c, double& d, double a, double b) {
-  const double p = __dmul_rd(a, b);
-  c += p;
-  d += fma(a, b, -p);
-}
-
-// App. A, the simpler procedure for ||a||^2 of complex data: one element's
-// term (e + the smaller c) + the larger c, e = d_re + d_im
-__device__ __forceinline__ double enh_abs2(double re, double im) {
-  const double cr = __dmul_rd(re, re), ci = __dmul_rd(im, im);
-  const double e = fma(re, re, -cr) + fma(im, im, -ci);
-  return cr <= ci ? (e + cr) + ci : (e + ci) + cr;
-}
-
 // ||y||^2 of column y (m elements, E scalars each) in shared memory, summed
 // by one warp: ordinary (fma) or enhanced; the result on every lane
 template <class T, bool CPLX, bool ENH>

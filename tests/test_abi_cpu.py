@@ -160,17 +160,20 @@ def test_size_limits_of_the_header(lib):
     assert lib.gsvd_workspace_bytes(ctypes.byref(cfg), 0, 40000, 40000, 32769) == 0
 
 
-def test_variants_plan_on_the_pointwise_kernel_only(lib):
+def test_variants_plan_where_the_pivot_step_has_them(lib):
     """Variants 1-3 of Sec. 2.6 (enhanced dots, D-hat rescaling) have a plan on
-    the pointwise kernel and none on the blocked path."""
+    the pointwise kernel and on the blocked path with real-view width V <= 32
+    (the two-CTA FP64 pivot step); none with V = 64 (w = 32, real)."""
     import paper_1909_00101_gb300 as hz
     for v in (1, 2, 3):
         cfg = hz.make_config(variant=v)
         assert lib.gsvd_workspace_bytes(ctypes.byref(cfg), 0, 64, 48, 32) > 0
         assert lib.gsvd_workspace_bytes(ctypes.byref(cfg), 1, 48, 40, 24) > 0
-        assert lib.gsvd_workspace_bytes(ctypes.byref(cfg), 0, 4096, 4096, 2048) == 0
+        assert lib.gsvd_workspace_bytes(ctypes.byref(cfg), 0, 4096, 4096, 2048) > 0
         blk = hz.make_config(variant=v, path="blocked")
-        assert lib.gsvd_workspace_bytes(ctypes.byref(blk), 0, 64, 48, 32) == 0
+        assert lib.gsvd_workspace_bytes(ctypes.byref(blk), 0, 64, 48, 32) > 0
+        wide = hz.make_config(variant=v, path="blocked", block_w=32)
+        assert lib.gsvd_workspace_bytes(ctypes.byref(wide), 0, 300, 300, 128) == 0
 
 
 def test_binding_structs_match_the_header(tmp_path):

@@ -158,6 +158,20 @@ def test_blocked_real_fp64(hz, w, shape, shorten):
     check(p.F, p.G, r, label="blocked w=%d %s shorten=%d" % (w, shape, shorten))
 
 
+@pytest.mark.parametrize("cplx,w", [(False, 8), (False, 16), (True, 4), (True, 8)])
+def test_blocked_apply_on_tcgen05(hz, cplx, w):
+    """fp64_gemm = 2: the block apply of the FP64 sweeps issued as
+    tcgen05.mma with the level sums in tensor memory (real-view widths 16 and
+    32, 128-row tiles), against the oracle, and bitwise repeatable."""
+    shape = (200, 180, 100) if not cplx else (120, 90, 72)
+    p = make_pair(*shape, lo=1e-3, hi=1e3, cond=1e2, cplx=cplx, seed=116 if not cplx else w)
+    r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", block_w=w, shorten=0, fp64_gemm=2)
+    check(p.F, p.G, r, label="tcgen05 apply cplx=%s w=%d" % (cplx, w))
+    q = hz.solve(_dev(p.F), _dev(p.G), path="blocked", block_w=w, shorten=0, fp64_gemm=2)
+    for a, b in ((r.sigma, q.sigma), (r.Z, q.Z), (r.U, q.U)):
+        assert torch.equal(a, b)
+
+
 @pytest.mark.parametrize("w", [4, 8, 16])
 def test_blocked_complex_fp64(hz, w):
     p = make_pair(120, 90, 72, lo=1e-3, hi=1e3, cond=1e2, cplx=True, seed=w)

@@ -1,6 +1,7 @@
 """GPU parity of the variants of Sec. 2.6 (Table "Variants") on the
-pointwise kernel: the enhanced dot products of App. A (+1), the D-hat
-rescaling (+2), and with criterion C2 the variants 4-7.  Each case runs the
+pointwise kernel and in the FP64 pivot step of the blocked path: the enhanced
+dot products of App. A (+1), the D-hat rescaling (+2), and with criterion C2
+the variants 4-7.  Each case runs the
 library through the C ABI and the oracle in the same variant, with the
 tolerance of the other parity tests (extended-precision oracle, R14 rule) and
 the invariants; the row-cyclic order follows the oracle's sequence.
@@ -98,7 +99,21 @@ def test_variants_in_a_batch_equal_single_solves(hz):
     s.close()
 
 
-def test_variants_refused_on_the_blocked_path(hz):
+@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_blocked_variants_match_the_oracle(hz, variant, cplx):
+    """The variants in the FP64 pivot step of the blocked path (the inner
+    level's dot products by App. A, the D-hat rescaling instead of the inner
+    prescale) give the oracle's GSVD in the same variant."""
+    p = make_pair(120, 100 if not cplx else 90, 72, lo=1e-3, hi=1e3, cond=1e2, cplx=cplx, seed=60 + variant)
+    r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", block_w=8 if not cplx else 4, shorten=0, variant=variant)
+    assert r.info["path"] == 2
+    _check(p, r, variant, "blocked %s" % ("complex" if cplx else "real"))
+
+
+def test_variants_refused_where_the_pivot_step_has_none(hz):
+    """Pair width 64 (w = 32, real) runs the one-CTA pivot step, which has
+    only variant 0: a variant there is refused before any launch."""
     p = make_pair(300, 300, 128, seed=5)
-    r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", variant=1)
+    r = hz.solve(_dev(p.F), _dev(p.G), path="blocked", block_w=32, variant=1)
     assert r.status == hz.EINVAL
