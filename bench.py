@@ -213,21 +213,43 @@ def steps_of(info, n):
 
 
 # DRAM bytes per launch of the sweep kernels at the benchmark's size, from one
-# ncu capture each (dram__bytes_read.sum + dram__bytes_write.sum; summaries
-# under profiles/); bytes per pair visit, scaled by the visits of a launch.
-# The figure holds for the kernel source it was taken on: each entry names
-# that source's SHA-256, and a changed source gives null.
-TRAFFIC = {}
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, 64 pair visits per
+# launch; profiles/sweep_kernels_dram_2048x2048.md): bytes per pair visit,
+# scaled by the visits of a launch.  A figure holds for the kernel it was taken
+# on: each entry names the SHA-256 of that kernel's source text, and a changed
+# kernel gives null.
+TRAFFIC = {
+    "gram_f64": {"kernel": "k_gram_oz", "source": "k_ozaki.cu", "bytes_per_visit": (67.16e6 + 0.01e6) / 64,
+                 "source_sha256": "860a1806e0ecd77257ef0138f7514488402a5ef23507740c9ae6d6b4e423b1a3"},
+    "inner_f64": {"kernel": "k_inner2", "source": "k_blocked.cu", "bytes_per_visit": 4.00e6 / 64,
+                  "source_sha256": "b637aa08c35fe57f6ea47b4e749c1ad9784d40529237f229aac3a104d2dfd617"},
+    "apply_f64": {"kernel": "k_apply_oz", "source": "k_ozaki.cu", "bytes_per_visit": (101.26e6 + 36.8e6) / 64,
+                  "source_sha256": "df068c29cfbc202a928c5549a43d4d568a8a10996b2a74d47d2d292db96071ea"},
+}
+
+
+def kernel_source_sha256(source, kernel):
+    """SHA-256 of a kernel's definition: from the line that declares it
+    (`... kernel(`) to the first line that closes it at column 0."""
+    import hashlib
+    with open(os.path.join(ROOT, "paper_1909_00101_gb300", "csrc", source)) as f:
+        lines = f.read().split("\n")
+    for i, ln in enumerate(lines):
+        if "__global__" in ln or (i > 0 and "__global__" in lines[i - 1]):
+            if (" %s(" % kernel) in ln or ln.strip().startswith(kernel + "("):
+                j = i
+                while j < len(lines) and lines[j] != "}":
+                    j += 1
+                return hashlib.sha256("\n".join(lines[i:j + 1]).encode()).hexdigest()
+    return None
 
 
 def traffic_per_launch(kernel, units):
     ent = TRAFFIC.get(kernel)
     if not ent:
         return None
-    import hashlib
-    with open(os.path.join(ROOT, "paper_1909_00101_gb300", "csrc", ent["source"]), "rb") as f:
-        if hashlib.sha256(f.read()).hexdigest() != ent["source_sha256"]:
-            return None
+    if kernel_source_sha256(ent["source"], ent["kernel"]) != ent["source_sha256"]:
+        return None
     return ent["bytes_per_visit"] * units
 
 

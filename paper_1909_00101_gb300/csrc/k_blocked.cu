@@ -151,14 +151,16 @@ __global__ void __launch_bounds__(gram_threads<T, V>()) k_gram(BlkDims d, BlkBuf
       out[i * V + j + 1] = acc[u][1];
     }
   } else {
-    constexpr int LDT = V + 1;
-    constexpr int NV = V / 16;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    float acc[NV][NV];
+    constexpr int LDT = V + 4;            // row stride of the staged tile (16-byte aligned rows)
+    constexpr int TPG = (V / 4) * (V / 4);  // threads of a row group: one 4 x 4 block of the Gram each
+    constexpr int NG = 256 / TPG;           // row groups: each sums its rows of the tile, then all add up
+    const int g = threadIdx.x / TPG, tq = threadIdx.x % TPG;
+    const int bi = 4 * (tq % (V / 4)), bj = 4 * (tq / (V / 4));
+    float acc[4][4];
 #pragma unroll
-    for (int u = 0; u < NV; ++u)
+    for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int v = 0; v < NV; ++v) acc[u][v] = 0.0f;
+      for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
     // the next row tile is prefetched into registers while this one is used
     constexpr int E = CPLX ? 2 : 1;
     constexpr int PERT = (V / E) * TR / 256;
@@ -195,27 +197,42 @@ __global__ void __launch_bounds__(gram_threads<T, V>()) k_gram(BlkDims d, BlkBuf
       }
       if (rt + TR < r1) fetch(rt + TR);
       __syncthreads();
+      // group g takes rows g, g + NG, ... of the tile; 8 loads, 16 FMAs a row
 #pragma unroll 4
-      for (int r = 0; r < TR; ++r) {
-        float a[NV], bv[NV];
+      for (int r = g; r < TR; r += NG) {
+        const float4 a = *reinterpret_cast<const float4*>(&Ws[r * LDT + bi]);
+        const float4 bv = *reinterpret_cast<const float4*>(&Ws[r * LDT + bj]);
+        const float av[4] = {a.x, a.y, a.z, a.w}, bw[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
-        for (int u = 0; u < NV; ++u) a[u] = Ws[r * LDT + tx + 16 * u];
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < NV; ++v) bv[v] = Ws[r * LDT + ty + 16 * v];
-#pragma unroll
-        for (int u = 0; u < NV; ++u)
-#pragma unroll
-          for (int v = 0; v < NV; ++v) acc[u][v] = fmaf(a[u], bv[v], acc[u][v]);
+          for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bw[v], acc[u][v]);
       }
       __syncthreads();
     }
-    // the real Gram is symmetric and acc[u][v] (entry (tx + 16u, ty + 16v))
-    // has the same bits as its mirror, so it is stored as entry
-    // (ty + 16v, tx + 16u): consecutive lanes write consecutive addresses
+    // the groups' partial Grams added in group order (a fixed order): group
+    // g's block goes through shared memory, group 0 sums and writes
+    float* part = Ws;  // reuse: the buffer holds (NG - 1) V x V floats (gram_smem)
+    if (g > 0) {
 #pragma unroll
-    for (int u = 0; u < NV; ++u)
+      for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int v = 0; v < NV; ++v) out[(ty + 16 * v) * V + tx + 16 * u] = acc[u][v];
+        for (int v = 0; v < 4; ++v) part[((g - 1) * V + bi + u) * V + bj + v] = acc[u][v];
+    }
+    __syncthreads();
+    if (g == 0) {
+      for (int gg = 1; gg < NG; ++gg)
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] += part[((gg - 1) * V + bi + u) * V + bj + v];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        float4 w4;
+        w4.x = acc[u][0]; w4.y = acc[u][1]; w4.z = acc[u][2]; w4.w = acc[u][3];
+        *reinterpret_cast<float4*>(&out[(bi + u) * V + bj]) = w4;
+      }
+    }
   }
 }
 
@@ -1472,8 +1489,114 @@ __global__ void __launch_bounds__(256) k_apply(BlkDims d, BlkBuffers b, int step
 
 template <class T, int V>
 size_t gram_smem() {
-  return std::is_same<T, double>::value ? sizeof(double) * V * (TR + 4) : sizeof(float) * TR * (V + 1);
+  // FP32: the staged row tile, or the row groups' partial Grams at the end
+  // (groups of (V/4)^2 threads, 256 / (V/4)^2 groups), whichever is larger
+  constexpr size_t tile32 = (size_t)TR * (V + 4), parts32 = (size_t)(256 / ((V / 4) * (V / 4)) - 1) * V * V;
+  return std::is_same<T, double>::value ? sizeof(double) * V * (TR + 4)
+                                        : sizeof(float) * (tile32 > parts32 ? tile32 : parts32);
 }
+// FP32 bulk sweeps: [Y_p Y_q] <- [Y_p Y_q] Z-tilde with one row of a 256-row
+// tile per thread: the row's V real-view values in registers, Z-tilde in
+// shared memory (read as broadcasts), V FMA chains per thread summed over k
+// in increasing order -- the arithmetic of the 64-row kernel, with no shared
+// staging of the tile and one Z-tilde load per 256 rows.
+constexpr int TR32 = 256;
+
+template <bool CPLX, int V>
+__global__ void __launch_bounds__(256, 2) k_apply32(BlkDims d, BlkBuffers b, int step, int tile0, BlkBatch bt) {
+  __shared__ __align__(16) float Ms[V * V];  // row-major Z-tilde (real view)
+  int slot;
+  if (!batch_item(bt, blockIdx.x, step, d, b, slot)) return;
+  PairCols pc;
+  if (!load_pair(d, b, step, slot, pc)) return;
+  if (!b.flags[slot]) return;
+  const int tf = (d.mf + TR32 - 1) / TR32, tg = (d.mg + TR32 - 1) / TR32;
+  int tile = tile0 + blockIdx.y;
+  if (tile >= tf + tg + (d.n + TR32 - 1) / TR32) return;
+  float* Y;
+  long long ld;
+  int m;
+  if (tile < tf) {
+    Y = static_cast<float*>(b.F); ld = b.ldf; m = d.mf;
+  } else if (tile < tf + tg) {
+    tile -= tf; Y = static_cast<float*>(b.G); ld = b.ldg; m = d.mg;
+  } else {
+    tile -= tf + tg; Y = static_cast<float*>(b.Z); ld = b.ldz; m = d.n;
+  }
+  const float* zt = static_cast<const float*>(b.ztil) + (size_t)slot * V * V;
+  for (int idx = threadIdx.x; idx < V * V; idx += blockDim.x) Ms[idx] = zt[idx];
+  const int bb = pc.bb;
+  const int r = tile * TR32 + threadIdx.x;
+  const bool live = r < m;
+  if constexpr (!CPLX) {
+    float y[V];
+#pragma unroll
+    for (int c = 0; c < V; ++c) y[c] = (live && c < bb) ? Y[(size_t)pc.gcol(c) * ld + r] : 0.0f;
+    __syncthreads();
+    float acc[V];
+#pragma unroll
+    for (int jj = 0; jj < V; ++jj) acc[jj] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      const float a = y[k];
+#pragma unroll
+      for (int j4 = 0; j4 < V; j4 += 4) {
+        const float4 z = *reinterpret_cast<const float4*>(&Ms[k * V + j4]);
+        acc[j4] = fmaf(a, z.x, acc[j4]);
+        acc[j4 + 1] = fmaf(a, z.y, acc[j4 + 1]);
+        acc[j4 + 2] = fmaf(a, z.z, acc[j4 + 2]);
+        acc[j4 + 3] = fmaf(a, z.w, acc[j4 + 3]);
+      }
+    }
+    if (!live) return;
+#pragma unroll
+    for (int c = 0; c < V; ++c)
+      if (c < bb) Y[(size_t)pc.gcol(c) * ld + r] = acc[c];
+  } else {
+    // real view: columns [0, bb) Re, [bb, 2 bb) Im, beyond zero; k runs over
+    // the Re rows of Z-tilde, then the Im rows
+    constexpr int H = V / 2;
+    float yr[H], yi[H];
+    const float2* Y2 = reinterpret_cast<const float2*>(Y);
+#pragma unroll
+    for (int c = 0; c < H; ++c) {
+      float2 v = make_float2(0.0f, 0.0f);
+      if (live && c < bb) v = Y2[(size_t)pc.gcol(c) * ld + r];
+      yr[c] = v.x;
+      yi[c] = v.y;
+    }
+    __syncthreads();
+    float ar[H], ai[H];  // output columns c (Re) and bb + c (Im)
+#pragma unroll
+    for (int c = 0; c < H; ++c) ar[c] = ai[c] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      if (k >= bb) break;
+      const float a = yr[k];
+#pragma unroll
+      for (int c = 0; c < H; ++c) {
+        ar[c] = fmaf(a, Ms[k * V + c], ar[c]);
+        ai[c] = fmaf(a, Ms[k * V + bb + c], ai[c]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      if (k >= bb) break;
+      const float a = yi[k];
+#pragma unroll
+      for (int c = 0; c < H; ++c) {
+        ar[c] = fmaf(a, Ms[(bb + k) * V + c], ar[c]);
+        ai[c] = fmaf(a, Ms[(bb + k) * V + bb + c], ai[c]);
+      }
+    }
+    if (!live) return;
+    float2* Yw = reinterpret_cast<float2*>(Y);
+#pragma unroll
+    for (int c = 0; c < H; ++c)
+      if (c < bb) Yw[(size_t)pc.gcol(c) * ld + r] = make_float2(ar[c], ai[c]);
+  }
+}
+
 template <class T, int V>
 size_t apply_smem() {
   return std::is_same<T, double>::value ? sizeof(double) * (V * (TR + 8) + V * (V + 8))
@@ -1509,6 +1632,21 @@ cudaError_t gram_v(const BlkDims& d, const BlkBuffers& b, int step, cudaStream_t
 template <class T, bool CPLX, int V>
 cudaError_t apply_v(const BlkDims& d, const BlkBuffers& b, int step, cudaStream_t s, const BlkBatch* bt, int nitems,
                     int grid_y) {
+  if constexpr (std::is_same<T, float>::value && V <= 32) {
+    const BlkBatch one;
+    auto kern32 = k_apply32<CPLX, V>;
+    if (bt) {  // batched: grid y sized for 64-row tiles; the extra blocks leave at once
+      kern32<<<dim3(nitems, grid_y), 256, 0, s>>>(d, b, step, 0, *bt);
+      return cudaGetLastError();
+    }
+    const int tiles = (d.mf + TR32 - 1) / TR32 + (d.mg + TR32 - 1) / TR32 + (d.n + TR32 - 1) / TR32;
+    for (int t0 = 0; t0 < tiles; t0 += 65535) {
+      kern32<<<dim3(d.nslots, std::min(65535, tiles - t0)), 256, 0, s>>>(d, b, step, t0, one);
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   const size_t smem = apply_smem<T, V>();
   auto kern = k_apply<T, CPLX, V>;
   cudaError_t e = set_smem(kern, smem);
