@@ -48,6 +48,14 @@ def measured_peaks():
         return 1900.0, "of fallback"
 
 
+def hbm_peak_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -584,8 +592,9 @@ def main():
     ap.add_argument("--max-sweeps", type=int, default=60)
     ap.add_argument("--fp32-params", type=int, default=None, choices=[0, 1],
                     help="2x2 parameters of the FP32 bulk sweeps in FP32 (1) or FP64 (0); default: library's")
-    ap.add_argument("--fp64-gemm", type=int, default=None, choices=[0, 1],
-                    help="FP64 Gram/apply on the BF16 tensor cores (1) or FP64 DMMA (0); default: library's")
+    ap.add_argument("--fp64-gemm", type=int, default=None, choices=[0, 1, 2],
+                    help="FP64 Gram/apply as exact BF16 slices on mma.sync (1), apply on tcgen05 (2), "
+                         "or FP64 DMMA (0); default: library's")
     ap.add_argument("--fp32-stop", type=int, default=None,
                     help="FP32 sweeps stop below this many per mille big transformations; default: library's")
     ap.add_argument("--shorten", type=int, default=1, choices=[0, 1, 2],
@@ -750,6 +759,16 @@ def main():
                                 % peak_note}
         if names[k].startswith("inner"):
             ent["note"] = "latency-bound: FP64 2x2 parameter chain per inner step, one CTA per pair visit"
+        elif not fp32 and (args.fp64_gemm if args.fp64_gemm is not None else 1) >= 1:
+            # the FP64 Gram and apply run as exact BF16 digit products on the
+            # tensor pipe: the FP64-equivalent rate may exceed the FP64 pipe's
+            # peak; the HBM fraction of the algorithmic bytes is given beside it
+            by = units * 8.0 * b * ((sm_f + sm_g) if names[k].startswith("gram") else 2.0 * (sm_f + sm_g + n))
+            ent["note"] = ("FP64-equivalent flops of exact BF16 digit products (36 per FP64 product): "
+                           "frac > 1 = faster than the FP64 pipe could do them; limited by the integer "
+                           "slicing and recombination")
+            ent["hbm"] = {"algorithmic_bytes_per_launch": by, "achieved_gbs": by / avg_s / 1e9,
+                          "frac": by / avg_s / 1e9 / hbm_peak_gbs(), "peak_note": "HBM copy %s" % peak_note}
         ent.update({"kernel": names[k], "avg_launch_us": avg_s * 1e6, "launches": int(nk[k]),
                     "units_per_launch": units, "flops_per_launch": flops})
         rooflines[names[k]] = ent
@@ -786,6 +805,10 @@ def main():
            "kernel_time_share": kshare,
            "kernel_time_source": "one profiled solve after the timed region (per-launch CUDA events on the "
                                  "solve's stream); the timed steps run without them",
+           "flop_convention": "per pair visit, pair width b = 2w, m = m_F + m_G (n x n factors when shortened): "
+                              "Gram b(b+1) m; apply 2 b^2 (m + n) per applied visit; inner 2 b^3/3 (two "
+                              "Choleskys) + b(b-1)/2 pivots x 32 b (four dots and six column updates of "
+                              "length b, real data)",
            "roofline": roof, "rooflines": rooflines, "clocks": clk,
            "gpu_launches": None}
     # launches of our kernels in the timed region: per sweep 3 per outer step

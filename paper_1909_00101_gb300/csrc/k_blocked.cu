@@ -1495,24 +1495,190 @@ size_t gram_smem() {
   return std::is_same<T, double>::value ? sizeof(double) * V * (TR + 4)
                                         : sizeof(float) * (tile32 > parts32 ? tile32 : parts32);
 }
-// FP32 bulk sweeps: [Y_p Y_q] <- [Y_p Y_q] Z-tilde with one row of a 256-row
-// tile per thread: the row's V real-view values in registers, Z-tilde in
-// shared memory (read as broadcasts), V FMA chains per thread summed over k
-// in increasing order -- the arithmetic of the 64-row kernel, with no shared
-// staging of the tile and one Z-tilde load per 256 rows.
-constexpr int TR32 = 256;
+// ---------------------------------------------------------- FP32 kernels ----
+// The FP32 bulk sweeps' Gram and apply for real-view widths V = 16 and 32:
+// tiles staged in shared memory column by column with 4-byte cp.async
+// (coalesced reads of the column-major operands, zero fill outside the
+// matrix and beyond the pair's columns), register blocks of 8 x 8 (Gram) and
+// 4 x 8 (apply) per thread so that one 16-byte shared load feeds 16 or 32
+// FMAs.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit32() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait32_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait32_0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Rows [rt, rt + NR) of the real view of [Y_p Y_q] into Ys (column c at
+// Ys[c * NR + r]), one source column per warp at a time: rows at or beyond
+// rend are zero-filled by the copy, columns beyond the pair are zeroed with
+// plain stores.  Complex column c < bb gives real-view columns c (Re) and
+// bb + c (Im); the real-view columns [E bb, V) are zero.
+template <bool CPLX, int V, int NR, int NW>
+__device__ __forceinline__ void stage32(float* Ys, const float* Y, long long ld, int rt, int rend,
+                                        const PairCols& pc) {
+  static_assert(NR % 32 == 0, "rows per stage");
+  constexpr int E = CPLX ? 2 : 1;
+  const int bb = pc.bb, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c = warp; c < bb; c += NW) {
+    const float* col = Y + (size_t)E * ((size_t)pc.gcol(c) * ld + rt);
+#pragma unroll
+    for (int q = 0; q < NR / 32; ++q) {
+      const int r = lane + 32 * q;
+      const bool ok = rt + r < rend;
+      if constexpr (!CPLX) {
+        cp_async4(&Ys[c * NR + r], ok ? col + r : Y, ok);
+      } else {
+        cp_async4(&Ys[c * NR + r], ok ? col + 2 * r : Y, ok);
+        cp_async4(&Ys[(bb + c) * NR + r], ok ? col + 2 * r + 1 : Y, ok);
+      }
+    }
+  }
+  for (int c = E * bb + warp; c < V; c += NW) {
+#pragma unroll
+    for (int q = 0; q < NR / 32; ++q) Ys[c * NR + lane + 32 * q] = 0.0f;
+  }
+}
+
+// Gram of a row slab: thread block (bi, bj), bi <= bj, of the (V/8)^2 8 x 8
+// blocks (the upper triangle is what the pivot step reads; diagonal blocks
+// are full); the 32 lanes of a warp take 4-row chunks of each staged tile,
+// R warps per block split the chunks further.  The lanes' sums meet in a
+// halving shuffle tree, the R warps' in shared memory (both in a fixed order).
+template <int V>
+struct Gram32Cfg {
+  static constexpr int NB = V / 8, NBT = NB * (NB + 1) / 2;
+  static constexpr int R = V == 16 ? 2 : 1;
+  static constexpr int THREADS = 32 * NBT * R;
+  static constexpr int NR = 128 * R;  // rows per stage: one 4-row chunk per lane
+};
 
 template <bool CPLX, int V>
-__global__ void __launch_bounds__(256, 2) k_apply32(BlkDims d, BlkBuffers b, int step, int tile0, BlkBatch bt) {
-  __shared__ __align__(16) float Ms[V * V];  // row-major Z-tilde (real view)
+__global__ void __launch_bounds__(Gram32Cfg<V>::THREADS, 1) k_gram32(BlkDims d, BlkBuffers b, int step, BlkBatch bt) {
+  using C = Gram32Cfg<V>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Ys = reinterpret_cast<float*>(smem_raw);  // [2][V][NR]; at the end [R-1][NBT][64] sums
+  int slot;
+  if (!batch_item(bt, blockIdx.x, step, d, b, slot)) return;
+  const int s = blockIdx.y;
+  if (s >= d.rf + d.rg) return;
+  PairCols pc;
+  if (!load_pair(d, b, step, slot, pc)) return;
+  const bool isF = s < d.rf;
+  const int m = isF ? d.mf : d.mg;
+  const int nsplit = isF ? d.rf : d.rg;
+  const int si = isF ? s : s - d.rf;
+  const int tiles = (m + TR - 1) / TR;
+  const int per = (tiles + nsplit - 1) / nsplit * TR;
+  const int r0 = si * per, r1 = min(m, r0 + per);
+  const float* Y = static_cast<const float*>(isF ? b.F : b.G);
+  const long long ld = isF ? b.ldf : b.ldg;
+  float* out = static_cast<float*>(b.partial) + ((size_t)slot * (d.rf + d.rg) + s) * V * V;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int blk = warp % C::NBT, rg = warp / C::NBT;
+  int bi = 0, bj = blk;
+  while (bj >= C::NB - bi) { bj -= C::NB - bi; ++bi; }
+  bj += bi;
+  const bool diag = bi == bj;
+  const int chunk = rg * 32 + lane;  // this thread's 4-row chunk of a stage
+
+  float x[64];  // x[8 u + v]: entry (8 bi + u, 8 bj + v) of this thread's rows
+#pragma unroll
+  for (int e = 0; e < 64; ++e) x[e] = 0.0f;
+
+  const int nst = r0 < r1 ? (r1 - r0 + C::NR - 1) / C::NR : 0;
+  if (nst > 0) stage32<CPLX, V, C::NR, C::THREADS / 32>(Ys, Y, ld, r0, r1, pc);
+  cp_async_commit32();
+  for (int st = 0; st < nst; ++st) {
+    float* cur = Ys + (st & 1) * V * C::NR;
+    if (st + 1 < nst)
+      stage32<CPLX, V, C::NR, C::THREADS / 32>(Ys + ((st + 1) & 1) * V * C::NR, Y, ld, r0 + (st + 1) * C::NR, r1, pc);
+    cp_async_commit32();
+    cp_async_wait32_1();
+    __syncthreads();
+    if (r0 + st * C::NR + 4 * chunk < r1) {
+      float4 a[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] = *reinterpret_cast<const float4*>(&cur[(8 * bi + u) * C::NR + 4 * chunk]);
+#pragma unroll
+      for (int v = 0; v < 8; ++v) {
+        const float4 bv = diag ? a[v] : *reinterpret_cast<const float4*>(&cur[(8 * bj + v) * C::NR + 4 * chunk]);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          float& xe = x[8 * u + v];
+          xe = fmaf(a[u].x, bv.x, xe);
+          xe = fmaf(a[u].y, bv.y, xe);
+          xe = fmaf(a[u].z, bv.z, xe);
+          xe = fmaf(a[u].w, bv.w, xe);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  cp_async_wait32_0();
+
+  // halving tree over the lanes: after the step with offset o, a lane keeps
+  // the half of its entries selected by its bit o; entry e = 8u + v ends on
+  // lane e / 2 (element e % 2)
+#pragma unroll
+  for (int lvl = 0; lvl < 5; ++lvl) {
+    const int o = 16 >> lvl, half = 32 >> lvl;
+    const bool hi = lane & o;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const float send = hi ? x[i] : x[i + half];
+      const float keep = hi ? x[i + half] : x[i];
+      x[i] = keep + __shfl_xor_sync(FULL, send, o);
+    }
+  }
+  const int e0 = 2 * lane, u = e0 >> 3, v = e0 & 7;
+  if constexpr (C::R > 1) {
+    float* red = Ys;  // the stage buffers are no longer read
+    __syncthreads();
+    if (rg > 0) {
+      red[((rg - 1) * C::NBT + blk) * 64 + e0] = x[0];
+      red[((rg - 1) * C::NBT + blk) * 64 + e0 + 1] = x[1];
+    }
+    __syncthreads();
+    if (rg == 0) {
+#pragma unroll
+      for (int g = 1; g < C::R; ++g) {
+        x[0] += red[((g - 1) * C::NBT + blk) * 64 + e0];
+        x[1] += red[((g - 1) * C::NBT + blk) * 64 + e0 + 1];
+      }
+    }
+  }
+  if (rg == 0) *reinterpret_cast<float2*>(&out[(8 * bi + u) * V + 8 * bj + v]) = make_float2(x[0], x[1]);
+}
+
+template <int V>
+constexpr size_t gram32_smem() {
+  return sizeof(float) * 2 * V * Gram32Cfg<V>::NR;
+}
+
+// FP32 bulk sweeps: [Y_p Y_q] <- [Y_p Y_q] Z-tilde on a tile of TRW rows;
+// thread (row group rg, column group cg) computes rows 4 rg + [0, 4) and
+// columns 8 cg + [0, 8) as sums over k in increasing order; the outputs go
+// back through shared memory so that the global stores are coalesced.
+template <int V>
+struct Apply32Cfg {
+  static constexpr int NCG = V / 8, NRG = 256 / NCG, TRW = 4 * NRG;
+};
+
+template <bool CPLX, int V>
+__global__ void __launch_bounds__(256, 3) k_apply32(BlkDims d, BlkBuffers b, int step, int tile0, BlkBatch bt) {
+  using C = Apply32Cfg<V>;
+  __shared__ __align__(16) float Ys[V * C::TRW];  // column-major tile (real view)
+  __shared__ __align__(16) float Ms[V * V];       // row-major Z-tilde (real view)
   int slot;
   if (!batch_item(bt, blockIdx.x, step, d, b, slot)) return;
   PairCols pc;
   if (!load_pair(d, b, step, slot, pc)) return;
   if (!b.flags[slot]) return;
-  const int tf = (d.mf + TR32 - 1) / TR32, tg = (d.mg + TR32 - 1) / TR32;
+  const int tf = (d.mf + C::TRW - 1) / C::TRW, tg = (d.mg + C::TRW - 1) / C::TRW;
   int tile = tile0 + blockIdx.y;
-  if (tile >= tf + tg + (d.n + TR32 - 1) / TR32) return;
+  if (tile >= tf + tg + (d.n + C::TRW - 1) / C::TRW) return;
   float* Y;
   long long ld;
   int m;
@@ -1523,77 +1689,54 @@ __global__ void __launch_bounds__(256, 2) k_apply32(BlkDims d, BlkBuffers b, int
   } else {
     tile -= tf + tg; Y = static_cast<float*>(b.Z); ld = b.ldz; m = d.n;
   }
+  const int rt = tile * C::TRW;
+  stage32<CPLX, V, C::TRW, 8>(Ys, Y, ld, rt, m, pc);
+  cp_async_commit32();
   const float* zt = static_cast<const float*>(b.ztil) + (size_t)slot * V * V;
   for (int idx = threadIdx.x; idx < V * V; idx += blockDim.x) Ms[idx] = zt[idx];
-  const int bb = pc.bb;
-  const int r = tile * TR32 + threadIdx.x;
-  const bool live = r < m;
-  if constexpr (!CPLX) {
-    float y[V];
+  cp_async_wait32_0();
+  __syncthreads();
+  const int rg = threadIdx.x % C::NRG, cg = threadIdx.x / C::NRG;
+  float acc[4][8];
 #pragma unroll
-    for (int c = 0; c < V; ++c) y[c] = (live && c < bb) ? Y[(size_t)pc.gcol(c) * ld + r] : 0.0f;
-    __syncthreads();
-    float acc[V];
+  for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int jj = 0; jj < V; ++jj) acc[jj] = 0.0f;
+    for (int v = 0; v < 8; ++v) acc[u][v] = 0.0f;
+#pragma unroll 8
+  for (int k = 0; k < V; ++k) {
+    const float4 y = *reinterpret_cast<const float4*>(&Ys[k * C::TRW + 4 * rg]);
+    const float4 z0 = *reinterpret_cast<const float4*>(&Ms[k * V + 8 * cg]);
+    const float4 z1 = *reinterpret_cast<const float4*>(&Ms[k * V + 8 * cg + 4]);
+    const float yv[4] = {y.x, y.y, y.z, y.w}, zv[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
 #pragma unroll
-    for (int k = 0; k < V; ++k) {
-      const float a = y[k];
+    for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int j4 = 0; j4 < V; j4 += 4) {
-        const float4 z = *reinterpret_cast<const float4*>(&Ms[k * V + j4]);
-        acc[j4] = fmaf(a, z.x, acc[j4]);
-        acc[j4 + 1] = fmaf(a, z.y, acc[j4 + 1]);
-        acc[j4 + 2] = fmaf(a, z.z, acc[j4 + 2]);
-        acc[j4 + 3] = fmaf(a, z.w, acc[j4 + 3]);
+      for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(yv[u], zv[v], acc[u][v]);
+  }
+  __syncthreads();  // every thread is done reading the tile
+#pragma unroll
+  for (int v = 0; v < 8; ++v)
+    *reinterpret_cast<float4*>(&Ys[(8 * cg + v) * C::TRW + 4 * rg]) =
+        make_float4(acc[0][v], acc[1][v], acc[2][v], acc[3][v]);
+  __syncthreads();
+  // one column per warp at a time, 128 bytes (complex: 256) per store
+  const int bb = pc.bb, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c = warp; c < bb; c += 8) {
+    if constexpr (!CPLX) {
+      float* col = Y + (size_t)pc.gcol(c) * ld + rt;
+#pragma unroll
+      for (int q = 0; q < C::TRW / 32; ++q) {
+        const int r = lane + 32 * q;
+        if (rt + r < m) col[r] = Ys[c * C::TRW + r];
+      }
+    } else {
+      float2* col = reinterpret_cast<float2*>(Y) + (size_t)pc.gcol(c) * ld + rt;
+#pragma unroll
+      for (int q = 0; q < C::TRW / 32; ++q) {
+        const int r = lane + 32 * q;
+        if (rt + r < m) col[r] = make_float2(Ys[c * C::TRW + r], Ys[(bb + c) * C::TRW + r]);
       }
     }
-    if (!live) return;
-#pragma unroll
-    for (int c = 0; c < V; ++c)
-      if (c < bb) Y[(size_t)pc.gcol(c) * ld + r] = acc[c];
-  } else {
-    // real view: columns [0, bb) Re, [bb, 2 bb) Im, beyond zero; k runs over
-    // the Re rows of Z-tilde, then the Im rows
-    constexpr int H = V / 2;
-    float yr[H], yi[H];
-    const float2* Y2 = reinterpret_cast<const float2*>(Y);
-#pragma unroll
-    for (int c = 0; c < H; ++c) {
-      float2 v = make_float2(0.0f, 0.0f);
-      if (live && c < bb) v = Y2[(size_t)pc.gcol(c) * ld + r];
-      yr[c] = v.x;
-      yi[c] = v.y;
-    }
-    __syncthreads();
-    float ar[H], ai[H];  // output columns c (Re) and bb + c (Im)
-#pragma unroll
-    for (int c = 0; c < H; ++c) ar[c] = ai[c] = 0.0f;
-#pragma unroll
-    for (int k = 0; k < H; ++k) {
-      if (k >= bb) break;
-      const float a = yr[k];
-#pragma unroll
-      for (int c = 0; c < H; ++c) {
-        ar[c] = fmaf(a, Ms[k * V + c], ar[c]);
-        ai[c] = fmaf(a, Ms[k * V + bb + c], ai[c]);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < H; ++k) {
-      if (k >= bb) break;
-      const float a = yi[k];
-#pragma unroll
-      for (int c = 0; c < H; ++c) {
-        ar[c] = fmaf(a, Ms[(bb + k) * V + c], ar[c]);
-        ai[c] = fmaf(a, Ms[(bb + k) * V + bb + c], ai[c]);
-      }
-    }
-    if (!live) return;
-    float2* Yw = reinterpret_cast<float2*>(Y);
-#pragma unroll
-    for (int c = 0; c < H; ++c)
-      if (c < bb) Yw[(size_t)pc.gcol(c) * ld + r] = make_float2(ar[c], ai[c]);
   }
 }
 
@@ -1620,6 +1763,16 @@ cudaError_t set_smem(K kern, size_t smem) {
 template <class T, bool CPLX, int V>
 cudaError_t gram_v(const BlkDims& d, const BlkBuffers& b, int step, cudaStream_t s, const BlkBatch* bt, int nitems,
                    int grid_y) {
+  if constexpr (std::is_same<T, float>::value && V <= 32) {
+    constexpr size_t smem32 = gram32_smem<V>();
+    auto kern32 = k_gram32<CPLX, V>;
+    cudaError_t e32 = set_smem(kern32, smem32);
+    if (e32 != cudaSuccess) return e32;
+    const BlkBatch one;
+    dim3 grid(bt ? nitems : d.nslots, bt ? grid_y : d.rf + d.rg);
+    kern32<<<grid, Gram32Cfg<V>::THREADS, smem32, s>>>(d, b, step, bt ? *bt : one);
+    return cudaGetLastError();
+  }
   const size_t smem = gram_smem<T, V>();
   auto kern = k_gram<T, CPLX, V>;
   cudaError_t e = set_smem(kern, smem);
@@ -1639,7 +1792,8 @@ cudaError_t apply_v(const BlkDims& d, const BlkBuffers& b, int step, cudaStream_
       kern32<<<dim3(nitems, grid_y), 256, 0, s>>>(d, b, step, 0, *bt);
       return cudaGetLastError();
     }
-    const int tiles = (d.mf + TR32 - 1) / TR32 + (d.mg + TR32 - 1) / TR32 + (d.n + TR32 - 1) / TR32;
+    constexpr int TRW = Apply32Cfg<V>::TRW;
+    const int tiles = (d.mf + TRW - 1) / TRW + (d.mg + TRW - 1) / TRW + (d.n + TRW - 1) / TRW;
     for (int t0 = 0; t0 < tiles; t0 += 65535) {
       kern32<<<dim3(d.nslots, std::min(65535, tiles - t0)), 256, 0, s>>>(d, b, step, t0, one);
       const cudaError_t e = cudaGetLastError();
