@@ -498,7 +498,7 @@ def serving(args, hz, out):
 
     def run(s, arrivals, keep=None):
         t0 = time.perf_counter()
-        pending, lat, ok, results = {}, [], 0, {}
+        pending, lat, ok, results, bad = {}, [], 0, {}, []
         k = 0
         while k < len(arrivals) or pending:
             now = time.perf_counter() - t0
@@ -513,9 +513,14 @@ def serving(args, hz, out):
                     kk, a, res = pending.pop(t)
                     lat.append(time.perf_counter() - t0 - a)
                     ok += st == 0
+                    if st != 0 and len(bad) < 20:
+                        q = int(order[kk])
+                        bad.append({"request": kk, "pair": q, "shape": list(pool[q].F.shape) + [pool[q].G.shape[0]],
+                                    "complex": bool(np.iscomplexobj(pool[q].F)), "status": int(st)})
                     if keep is not None and kk in keep:
                         results[kk] = res.sigma.cpu().numpy()
             time.sleep(0.0002)
+        run.bad = bad
         return time.perf_counter() - t0, lat, ok, results
 
     solvers = {prec: hz.Solver(precision=prec, inner_max_sweeps=1, max_sweeps=80, fp32_max_sweeps=80,
@@ -543,6 +548,8 @@ def serving(args, hz, out):
             ent = {"lambda_per_s": lam, "solves_per_s": R / T, "ok": ok,
                    "latency_ms_p50": 1e3 * float(np.percentile(lat, 50)),
                    "latency_ms_p99": 1e3 * float(np.percentile(lat, 99))}
+            if run.bad:
+                ent["failed_requests"] = run.bad
             if prec == "mixed" and frac == args.loads[0] and keep:
                 ctx = mp.get_context("spawn")
                 cores = len(os.sched_getaffinity(0))
@@ -553,7 +560,10 @@ def serving(args, hz, out):
                 good = [c for c in chk if c[1] is not None]
                 out["oracle_check"] = {"requests": len(jobs), "cores": cores, "seconds": time.perf_counter() - t0,
                                        "bins_n": bins, "max_err_vs_oracle_ext": max(c[1] for c in good),
-                                       "all_within_tolerance": all(c[1] <= c[2] for c in good)}
+                                       "all_within_tolerance": all(c[1] <= c[2] for c in good),
+                                       "outside_tolerance": [{"request": c[0], "pair": int(order[c[0]]),
+                                                              "err": c[1], "tol": c[2]}
+                                                             for c in good if c[1] > c[2]]}
             arms[prec]["load_%.2f" % frac] = ent
     for s in solvers.values():
         s.close()

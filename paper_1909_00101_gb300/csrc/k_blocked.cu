@@ -245,6 +245,35 @@ template <class Ti>
 struct PivInT {
   Ti a11, a22, ar, ai, br, bi;
 };
+// Sums over the 16 lanes of a half-warp (both halves at once, each its own
+// values), in a fixed order.  half_sum4_all leaves all four sums in every
+// lane of the half: a transposing butterfly (offsets 8 and 4 halve the
+// values, 2 and 1 finish), then one broadcast per sum.
+__device__ __forceinline__ void half_sum4_all(float v[4]) {
+  const int lane = threadIdx.x & 31;
+  const bool b8 = lane & 8, b4 = lane & 4;
+  const float s0 = b8 ? v[0] : v[2], s1 = b8 ? v[1] : v[3];
+  float k0 = b8 ? v[2] : v[0], k1 = b8 ? v[3] : v[1];
+  k0 += __shfl_xor_sync(FULL, s0, 8);
+  k1 += __shfl_xor_sync(FULL, s1, 8);
+  const float sx = b4 ? k0 : k1;
+  float k = b4 ? k1 : k0;
+  k += __shfl_xor_sync(FULL, sx, 4);
+  k += __shfl_xor_sync(FULL, k, 2);
+  k += __shfl_xor_sync(FULL, k, 1);
+  // lanes 0-3 of the half hold sum 0, 4-7 sum 1, 8-11 sum 2, 12-15 sum 3
+  const int base = lane & 16;
+  v[0] = __shfl_sync(FULL, k, base);
+  v[1] = __shfl_sync(FULL, k, base + 4);
+  v[2] = __shfl_sync(FULL, k, base + 8);
+  v[3] = __shfl_sync(FULL, k, base + 12);
+}
+__device__ __forceinline__ float half_sum(float v) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
 template <class Ti>
 struct PivZ {
   Ti z11, z12, z21, z22, z12i, z21i;
@@ -353,16 +382,16 @@ __global__ void __launch_bounds__(INNER_THREADS) k_inner(BlkDims d, BlkBuffers b
   }
   __syncthreads();
 
-  // 2. Choleskys A-hat = R^* R and B-hat = R^* R (upper R) side by side: the
-  //    pivot of A on warp 0 and of B on warp 1 (two SM sub-partitions; the
-  //    pivot chain is the serial part), 1/sqrt from one rsqrt; the trailing
-  //    updates of both as packed lists.  FP64: the row k of R is scaled in
-  //    its own pass before the update (one FP64 multiply per entry); FP32:
-  //    the update scales the two row entries it reads and the row itself is
-  //    scaled while the next pivot is taken (same products, one barrier
-  //    less).  A non-positive pivot fails the visit.  Strict lower
-  //    triangles are not read afterwards (zeroed in step 3).
-  auto update = [&](int k, bool scaled) {
+  // 2. Choleskys A-hat = R^* R and B-hat = R^* R (upper R) side by side,
+  //    1/sqrt from one rsqrt, the trailing updates as packed lists.  FP32:
+  //    one warp per matrix, warp barriers only; the update scales the two
+  //    row entries it reads, then the row is stored scaled.  FP64: the pivots
+  //    of A and B on warps 0 and 1 (two SM sub-partitions; the pivot chain is
+  //    the serial part), the row k of R scaled in its own pass before the
+  //    block-wide update (one FP64 multiply per entry).  A non-positive pivot
+  //    fails the visit.  Strict lower triangles are not read afterwards
+  //    (zeroed in step 3).
+  auto update = [&](int k) {  // row k already scaled
     const int rem = bb - k - 1;
     const int nrem = rem * (rem + 1) / 2;
     for (int t = threadIdx.x; t < 2 * nrem; t += blockDim.x) {
@@ -370,16 +399,12 @@ __global__ void __launch_bounds__(INNER_THREADS) k_inner(BlkDims d, BlkBuffers b
       const int ij = s_tri[t - mat * nrem];
       const int i = k + 1 + (ij & 255), j = k + 1 + (ij >> 8);
       Tc* M = mat ? Bm : A;
-      const Tc sc = scaled ? Tc(1) : s_inv[mat];
       if constexpr (!CPLX) {
-        Tc rki = M[i * BMAX + k], rkj = M[j * BMAX + k];
-        if (!scaled) { rki *= sc; rkj *= sc; }
-        M[j * BMAX + i] = p_fma(-rki, rkj, M[j * BMAX + i]);
+        M[j * BMAX + i] = p_fma(-M[i * BMAX + k], M[j * BMAX + k], M[j * BMAX + i]);
       } else {
         // M_ij -= conj(R_ki) R_kj
-        Tc kir = M[2 * (i * BMAX + k)], kii = M[2 * (i * BMAX + k) + 1];
-        Tc kjr = M[2 * (j * BMAX + k)], kji = M[2 * (j * BMAX + k) + 1];
-        if (!scaled) { kir *= sc; kii *= sc; kjr *= sc; kji *= sc; }
+        const Tc kir = M[2 * (i * BMAX + k)], kii = M[2 * (i * BMAX + k) + 1];
+        const Tc kjr = M[2 * (j * BMAX + k)], kji = M[2 * (j * BMAX + k) + 1];
         M[2 * (j * BMAX + i)] -= kir * kjr + kii * kji;
         M[2 * (j * BMAX + i) + 1] -= kir * kji - kii * kjr;
       }
@@ -396,7 +421,89 @@ __global__ void __launch_bounds__(INNER_THREADS) k_inner(BlkDims d, BlkBuffers b
       if constexpr (CPLX) M[E * (j * BMAX + k) + 1] *= inv;
     }
   };
-  Tc prev0 = Tc(0), prev1 = Tc(0);  // FP32: pivots of the row still to scale
+  if constexpr (P32) {
+    // FP32: each matrix on one warp (A on warp 0, B on warp 1) with warp
+    // barriers only.  Lane l holds rows l, l + 32, ...; at step k it updates
+    // its rows' entries of every column j > k, reading row k's entry of
+    // column j as a broadcast (the products of the block-wide form below:
+    // both row-k factors scaled by 1/sqrt(pivot), then one fma), then stores
+    // its own entries of row k scaled.
+    constexpr int RPL = (BMAX + 31) / 32;
+    if (warp < 2) {
+      Tc* M = warp ? Bm : A;
+      bool bad = false;
+      for (int k = 0; k < bb; ++k) {
+        const Tc dkk = M[E * (k * BMAX + k)];
+        if (!(dkk > Tc(0)) || !isfinite(dkk)) {
+          bad = true;
+          break;
+        }
+        const Tc inv = p_rsqrt(dkk);
+        Tc rr[RPL], ri[RPL];  // R_ki of this lane's rows i (scaled)
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+          const int ir = lane + 32 * q;
+          rr[q] = ri[q] = Tc(0);
+          if (ir > k && ir < bb) {
+            rr[q] = M[E * (ir * BMAX + k)] * inv;
+            if constexpr (CPLX) ri[q] = M[E * (ir * BMAX + k) + 1] * inv;
+          }
+        }
+        // columns in groups of CG: all loads of a group before its stores
+        constexpr int CG = CPLX ? 4 : 8;
+        for (int j0 = k + 1; j0 < bb; j0 += CG) {
+          Tc kjr[CG], kji[CG], mr[RPL][CG], mi[RPL][CG];
+#pragma unroll
+          for (int u = 0; u < CG; ++u) {
+            const int jc = j0 + u;
+            kjr[u] = kji[u] = Tc(0);
+            if (jc < bb) {
+              kjr[u] = M[E * (jc * BMAX + k)] * inv;
+              if constexpr (CPLX) kji[u] = M[E * (jc * BMAX + k) + 1] * inv;
+            }
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) {
+              const int ir = lane + 32 * q;
+              mr[q][u] = mi[q][u] = Tc(0);
+              if (ir > k && ir <= jc && jc < bb) {
+                mr[q][u] = M[E * (jc * BMAX + ir)];
+                if constexpr (CPLX) mi[q][u] = M[E * (jc * BMAX + ir) + 1];
+              }
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < CG; ++u) {
+            const int jc = j0 + u;
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) {
+              const int ir = lane + 32 * q;
+              if (ir > k && ir <= jc && jc < bb) {
+                if constexpr (!CPLX) {
+                  M[jc * BMAX + ir] = p_fma(-rr[q], kjr[u], mr[q][u]);
+                } else {
+                  M[2 * (jc * BMAX + ir)] = mr[q][u] - (rr[q] * kjr[u] + ri[q] * kji[u]);
+                  M[2 * (jc * BMAX + ir) + 1] = mi[q][u] - (rr[q] * kji[u] - ri[q] * kjr[u]);
+                }
+              }
+            }
+          }
+        }
+        __syncwarp();  // every lane has read row k
+        if (lane == 0) M[E * (k * BMAX + k)] = dkk * inv;
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+          const int ir = lane + 32 * q;
+          if (ir > k && ir < bb) {
+            M[E * (ir * BMAX + k)] = rr[q];
+            if constexpr (CPLX) M[E * (ir * BMAX + k) + 1] = ri[q];
+          }
+        }
+        __syncwarp();
+      }
+      if (bad && lane == 0) s_bad = 1;
+    }
+    __syncthreads();
+  } else
   for (int k = 0; k < bb; ++k) {
     if (threadIdx.x == 0 || threadIdx.x == 32) {
       const int mat = threadIdx.x >> 5;
@@ -411,21 +518,11 @@ __global__ void __launch_bounds__(INNER_THREADS) k_inner(BlkDims d, BlkBuffers b
         s_inv[mat] = inv;
       }
     }
-    if constexpr (P32) {
-      if (k > 0) scale_row(k - 1, prev0, prev1);  // row k-1: not read by pivot k
-    }
     __syncthreads();
     if (s_bad) break;
-    if constexpr (P32) {
-      prev0 = s_inv[0];
-      prev1 = s_inv[1];
-      update(k, false);
-      if (k == bb - 1) scale_row(k, prev0, prev1);  // empty (no entries right of the last pivot)
-    } else {
-      scale_row(k, s_inv[0], s_inv[1]);
-      __syncthreads();
-      update(k, true);
-    }
+    scale_row(k, s_inv[0], s_inv[1]);
+    __syncthreads();
+    update(k);
     __syncthreads();
   }
   if (s_bad) {
@@ -490,44 +587,59 @@ __global__ void __launch_bounds__(INNER_THREADS) k_inner(BlkDims d, BlkBuffers b
   for (int sw = 0; sw < prm.inner_max; ++sw) {
     int sweep_all = 0;
     if constexpr (P32) {
-      // FP32 sweeps: each pair's warp takes its own 2x2 parameters (all lanes
-      // hold the four dot products after the reduction and compute the same
-      // FP32 values), so a step needs one barrier; counters per warp
+      // FP32 sweeps: one pair per half-warp (16 lanes; rows hl, hl + 16):
+      // both halves of a warp form their pair's dot products, take its 2x2
+      // parameters (every lane of the half the same FP32 values) and update
+      // its columns in the same instructions, so a step issues half the
+      // instructions of a warp per pair; one barrier per step; counters per
+      // half-warp
       int n_rot = 0, n_big = 0;
       bool chg = false;
       const float tolf = (float)tol;
+      const int hl = lane & 15;
       for (int st = 0; st < M - 1; ++st) {
-        for (int k = warp; k < npairs; k += nwarps) {
-          const int i = s_pair[st][k][0], j = s_pair[st][k][1];
-          if (j >= bb) continue;
+        for (int kb = 2 * warp; kb < npairs; kb += 2 * nwarps) {
+          const int k = kb + (lane >> 4);
+          int i = 0, j = 0;
+          bool valid = false;
+          if (k < npairs) {
+            i = s_pair[st][k][0];
+            j = s_pair[st][k][1];
+            valid = j < bb;
+          }
           float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
           float w2[2] = {0.0f, 0.0f};
           if constexpr (!CPLX) {
-            for (int r = lane; r < bb; r += 32) {
-              const float fi = Fh[i * bb + r], fj = Fh[j * bb + r];
-              v[0] += fi * fi;
-              v[1] += fj * fj;
-              v[2] += fi * fj;
-              v[3] += Gh[i * bb + r] * Gh[j * bb + r];
+            if (valid) {
+              for (int r = hl; r < bb; r += 16) {
+                const float fi = Fh[i * bb + r], fj = Fh[j * bb + r];
+                v[0] += fi * fi;
+                v[1] += fj * fj;
+                v[2] += fi * fj;
+                v[3] += Gh[i * bb + r] * Gh[j * bb + r];
+              }
             }
-            warp_sum4(v);
+            half_sum4_all(v);
           } else {
-            for (int r = lane; r < bb; r += 32) {
-              const float fir = Fh[2 * (i * bb + r)], fii = Fh[2 * (i * bb + r) + 1];
-              const float fjr = Fh[2 * (j * bb + r)], fji = Fh[2 * (j * bb + r) + 1];
-              const float gir = Gh[2 * (i * bb + r)], gii = Gh[2 * (i * bb + r) + 1];
-              const float gjr = Gh[2 * (j * bb + r)], gji = Gh[2 * (j * bb + r) + 1];
-              v[0] += fir * fir + fii * fii;
-              v[1] += fjr * fjr + fji * fji;
-              v[2] += fir * fjr + fii * fji;
-              v[3] += fir * fji - fii * fjr;
-              w2[0] += gir * gjr + gii * gji;
-              w2[1] += gir * gji - gii * gjr;
+            if (valid) {
+              for (int r = hl; r < bb; r += 16) {
+                const float fir = Fh[2 * (i * bb + r)], fii = Fh[2 * (i * bb + r) + 1];
+                const float fjr = Fh[2 * (j * bb + r)], fji = Fh[2 * (j * bb + r) + 1];
+                const float gir = Gh[2 * (i * bb + r)], gii = Gh[2 * (i * bb + r) + 1];
+                const float gjr = Gh[2 * (j * bb + r)], gji = Gh[2 * (j * bb + r) + 1];
+                v[0] += fir * fir + fii * fii;
+                v[1] += fjr * fjr + fji * fji;
+                v[2] += fir * fjr + fii * fji;
+                v[3] += fir * fji - fii * fjr;
+                w2[0] += gir * gjr + gii * gji;
+                w2[1] += gir * gji - gii * gjr;
+              }
             }
-            warp_sum4(v);
-            w2[0] = warp_sum(w2[0]);
-            w2[1] = warp_sum(w2[1]);
+            half_sum4_all(v);
+            w2[0] = half_sum(w2[0]);
+            w2[1] = half_sum(w2[1]);
           }
+          if (!valid) continue;
           PivotOutT<float> o;
           if constexpr (!CPLX)
             o = pivot_real<float>(v[0], v[1], v[2], v[3], tolf, false, true, prm.crit2);
@@ -536,7 +648,7 @@ __global__ void __launch_bounds__(INNER_THREADS) k_inner(BlkDims d, BlkBuffers b
           const bool rot = o.flags & PV_ROT;
           bool swp = o.flags & PV_SWAP;
           if (o.flags & PV_FAIL) {
-            if (lane == 0) s_ctr[2] = 1;
+            if (hl == 0) s_ctr[2] = 1;
             continue;
           }
           if constexpr (!CPLX) {
@@ -557,7 +669,7 @@ __global__ void __launch_bounds__(INNER_THREADS) k_inner(BlkDims d, BlkBuffers b
           if (!rot && !swp) continue;
           const float z11 = o.z11, z12 = o.z12, z21 = o.z21, z22 = o.z22, z12i = o.z12i, z21i = o.z21i;
           auto upd = [&](float* Y) {
-            for (int r = lane; r < bb; r += 32) {
+            for (int r = hl; r < bb; r += 16) {
               if constexpr (!CPLX) {
                 const float yi = Y[i * bb + r], yj = Y[j * bb + r];
                 float ni = yi, nj = yj;
@@ -591,7 +703,7 @@ __global__ void __launch_bounds__(INNER_THREADS) k_inner(BlkDims d, BlkBuffers b
         __syncthreads();
         if (s_ctr[2]) break;
       }
-      if (lane == 0) {
+      if (hl == 0) {
         if (n_rot) atomicAdd(&s_ctr[0], n_rot);
         if (n_big) atomicAdd(&s_ctr[1], n_big);
         if (chg) s_ctr[3] = 1;
@@ -1551,7 +1663,8 @@ struct Gram32Cfg {
   static constexpr int NB = V / 8, NBT = NB * (NB + 1) / 2;
   static constexpr int R = V == 16 ? 2 : 1;
   static constexpr int THREADS = 32 * NBT * R;
-  static constexpr int NR = 128 * R;  // rows per stage: one 4-row chunk per lane
+  static constexpr int CPL = 2;             // 4-row chunks per lane and stage
+  static constexpr int NR = 128 * R * CPL;  // rows per stage
 };
 
 template <bool CPLX, int V>
@@ -1581,7 +1694,7 @@ __global__ void __launch_bounds__(Gram32Cfg<V>::THREADS, 1) k_gram32(BlkDims d, 
   while (bj >= C::NB - bi) { bj -= C::NB - bi; ++bi; }
   bj += bi;
   const bool diag = bi == bj;
-  const int chunk = rg * 32 + lane;  // this thread's 4-row chunk of a stage
+  const int chunk0 = rg * 32 + lane;  // this thread's 4-row chunks of a stage: chunk0 + 32 R c
 
   float x[64];  // x[8 u + v]: entry (8 bi + u, 8 bj + v) of this thread's rows
 #pragma unroll
@@ -1597,7 +1710,10 @@ __global__ void __launch_bounds__(Gram32Cfg<V>::THREADS, 1) k_gram32(BlkDims d, 
     cp_async_commit32();
     cp_async_wait32_1();
     __syncthreads();
-    if (r0 + st * C::NR + 4 * chunk < r1) {
+#pragma unroll
+    for (int cc = 0; cc < C::CPL; ++cc) {
+      const int chunk = chunk0 + 32 * C::R * cc;
+      if (r0 + st * C::NR + 4 * chunk >= r1) break;
       float4 a[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) a[u] = *reinterpret_cast<const float4*>(&cur[(8 * bi + u) * C::NR + 4 * chunk]);
