@@ -233,6 +233,12 @@ TRAFFIC = {
                   "source_sha256": "b637aa08c35fe57f6ea47b4e749c1ad9784d40529237f229aac3a104d2dfd617"},
     "apply_f64": {"kernel": "k_apply_oz", "source": "k_ozaki.cu", "bytes_per_visit": (101.26e6 + 36.8e6) / 64,
                   "source_sha256": "df068c29cfbc202a928c5549a43d4d568a8a10996b2a74d47d2d292db96071ea"},
+    "gram_f32": {"kernel": "k_gram32", "source": "k_blocked.cu", "bytes_per_visit": 33.58e6 / 64,
+                 "source_sha256": "57e668b5be7f57d6eb8bfbbe721f290317d8ca6ed6d9958b7dd74bdb2bdd7339"},
+    "inner_f32": {"kernel": "k_inner", "source": "k_blocked.cu", "bytes_per_visit": 2.668e6 / 64,
+                  "source_sha256": "f98af51cefa4c80de6b1f7b6834fb62a85ce560ce21c838ec6356e11a2c43ba8"},
+    "apply_f32": {"kernel": "k_apply32", "source": "k_blocked.cu", "bytes_per_visit": (50.61e6 + 0.04e6) / 64,
+                  "source_sha256": "cb02e515db0e5c8e01f6a67a79bcfb0a30b20d850750175c357073c6f327a158"},
 }
 
 
@@ -767,8 +773,12 @@ def main():
                    "frac": ach / fp64_peak, "traffic": tr,
                    "peak_note": "FP64 pipe (DMMA issues on it): bf16 dense %s x 1.25/2250 nominal FP64/bf16"
                                 % peak_note}
-        if names[k].startswith("inner"):
-            ent["note"] = "latency-bound: FP64 2x2 parameter chain per inner step, one CTA per pair visit"
+        if names[k] == "inner_f64":
+            ent["note"] = ("latency-bound: 31 dependent inner steps per pair visit, each an FP64 2x2 parameter "
+                           "chain and a cluster barrier; two CTAs per pair visit")
+        elif names[k] == "inner_f32":
+            ent["note"] = ("latency-bound: two Choleskys and 31 dependent inner steps per pair visit (FP32 "
+                           "parameters, one pair per half-warp); one CTA per pair visit, 64 of 152 SMs")
         elif not fp32 and (args.fp64_gemm if args.fp64_gemm is not None else 1) >= 1:
             # the FP64 Gram and apply run as exact BF16 digit products on the
             # tensor pipe: the FP64-equivalent rate may exceed the FP64 pipe's
