@@ -641,10 +641,17 @@ __global__ void __launch_bounds__(INNER_THREADS) k_inner(BlkDims d, BlkBuffers b
           }
           if (!valid) continue;
           PivotOutT<float> o;
-          if constexpr (!CPLX)
-            o = pivot_real<float>(v[0], v[1], v[2], v[3], tolf, false, true, prm.crit2);
-          else
+          if constexpr (!CPLX) {
+            // the two chains of the real parameters have independent inputs:
+            // both issued here, they overlap (chain B is not used unless
+            // chain A rotates, which is what pivot_real computes)
+            const RealChainAT<float> ra = real_chain_a(v[0], v[1], v[2], v[3], tolf);
+            float xi, eta;
+            real_chain_b(v[3], xi, eta);
+            o = real_combine(v[0], v[1], v[2], v[3], ra, xi, eta, false, true, prm.crit2);
+          } else {
             o = pivot_cplx<float>(v[0], v[1], v[2], v[3], w2[0], w2[1], tolf, prm.sort, true, prm.crit2);
+          }
           const bool rot = o.flags & PV_ROT;
           bool swp = o.flags & PV_SWAP;
           if (o.flags & PV_FAIL) {
@@ -668,37 +675,53 @@ __global__ void __launch_bounds__(INNER_THREADS) k_inner(BlkDims d, BlkBuffers b
           chg = chg || rot || swp;
           if (!rot && !swp) continue;
           const float z11 = o.z11, z12 = o.z12, z21 = o.z21, z22 = o.z22, z12i = o.z12i, z21i = o.z21i;
-          auto upd = [&](float* Y) {
-            for (int r = hl; r < bb; r += 16) {
-              if constexpr (!CPLX) {
-                const float yi = Y[i * bb + r], yj = Y[j * bb + r];
-                float ni = yi, nj = yj;
+          // the three matrices' operands of a row are loaded before any of
+          // them is stored (shared loads are not reordered past stores that
+          // may alias)
+          float* Ym[3] = {reinterpret_cast<float*>(Fh), reinterpret_cast<float*>(Gh), reinterpret_cast<float*>(Zh)};
+          for (int r = hl; r < bb; r += 16) {
+            if constexpr (!CPLX) {
+              float yi[3], yj[3];
+#pragma unroll
+              for (int mm = 0; mm < 3; ++mm) {
+                yi[mm] = Ym[mm][i * bb + r];
+                yj[mm] = Ym[mm][j * bb + r];
+              }
+#pragma unroll
+              for (int mm = 0; mm < 3; ++mm) {
+                float ni = yi[mm], nj = yj[mm];
                 if (rot) {
-                  ni = fmaf(yj, z21, yi * z11);
-                  nj = fmaf(yi, z12, yj * z22);
+                  ni = fmaf(yj[mm], z21, yi[mm] * z11);
+                  nj = fmaf(yi[mm], z12, yj[mm] * z22);
                 }
-                Y[i * bb + r] = swp ? nj : ni;
-                Y[j * bb + r] = swp ? ni : nj;
-              } else {
-                const float yir = Y[2 * (i * bb + r)], yii = Y[2 * (i * bb + r) + 1];
-                const float yjr = Y[2 * (j * bb + r)], yji = Y[2 * (j * bb + r) + 1];
-                float nir = yir, nii = yii, njr = yjr, nji = yji;
+                Ym[mm][i * bb + r] = swp ? nj : ni;
+                Ym[mm][j * bb + r] = swp ? ni : nj;
+              }
+            } else {
+              float yir[3], yii[3], yjr[3], yji[3];
+#pragma unroll
+              for (int mm = 0; mm < 3; ++mm) {
+                yir[mm] = Ym[mm][2 * (i * bb + r)];
+                yii[mm] = Ym[mm][2 * (i * bb + r) + 1];
+                yjr[mm] = Ym[mm][2 * (j * bb + r)];
+                yji[mm] = Ym[mm][2 * (j * bb + r) + 1];
+              }
+#pragma unroll
+              for (int mm = 0; mm < 3; ++mm) {
+                float nir = yir[mm], nii = yii[mm], njr = yjr[mm], nji = yji[mm];
                 if (rot) {
-                  nir = fmaf(yjr, z21, fmaf(-yji, z21i, yir * z11));
-                  nii = fmaf(yjr, z21i, fmaf(yji, z21, yii * z11));
-                  njr = fmaf(yir, z12, fmaf(-yii, z12i, yjr * z22));
-                  nji = fmaf(yir, z12i, fmaf(yii, z12, yji * z22));
+                  nir = fmaf(yjr[mm], z21, fmaf(-yji[mm], z21i, yir[mm] * z11));
+                  nii = fmaf(yjr[mm], z21i, fmaf(yji[mm], z21, yii[mm] * z11));
+                  njr = fmaf(yir[mm], z12, fmaf(-yii[mm], z12i, yjr[mm] * z22));
+                  nji = fmaf(yir[mm], z12i, fmaf(yii[mm], z12, yji[mm] * z22));
                 }
-                Y[2 * (i * bb + r)] = swp ? njr : nir;
-                Y[2 * (i * bb + r) + 1] = swp ? nji : nii;
-                Y[2 * (j * bb + r)] = swp ? nir : njr;
-                Y[2 * (j * bb + r) + 1] = swp ? nii : nji;
+                Ym[mm][2 * (i * bb + r)] = swp ? njr : nir;
+                Ym[mm][2 * (i * bb + r) + 1] = swp ? nji : nii;
+                Ym[mm][2 * (j * bb + r)] = swp ? nir : njr;
+                Ym[mm][2 * (j * bb + r) + 1] = swp ? nii : nji;
               }
             }
-          };
-          upd(reinterpret_cast<float*>(Fh));
-          upd(reinterpret_cast<float*>(Gh));
-          upd(reinterpret_cast<float*>(Zh));
+          }
         }
         __syncthreads();
         if (s_ctr[2]) break;
