@@ -422,86 +422,91 @@ __global__ void __launch_bounds__(INNER_THREADS) k_inner(BlkDims d, BlkBuffers b
     }
   };
   if constexpr (P32) {
-    // FP32: each matrix on one warp (A on warp 0, B on warp 1) with warp
-    // barriers only.  Lane l holds rows l, l + 32, ...; at step k it updates
-    // its rows' entries of every column j > k, reading row k's entry of
-    // column j as a broadcast (the products of the block-wide form below:
-    // both row-k factors scaled by 1/sqrt(pivot), then one fma), then stores
-    // its own entries of row k scaled.
+    // FP32: eight warps per matrix (A on warps 0-7, B on warps 8-15), one
+    // named barrier of the eight per step.  Lane l holds rows l, l + 32, ...;
+    // warp w of a matrix updates the columns j = w (mod 8) beyond k: its
+    // rows' entries of column j, with row k's entry of column j read as a
+    // broadcast (the products of the block-wide form below: both row-k
+    // factors scaled by 1/sqrt(pivot), then one fma).  After the barrier
+    // each warp stores row k's entries of its columns scaled; the next step
+    // reads only row k + 1 and its pivot, which the barrier has published.
+    static_assert(INNER_THREADS == 512, "eight warps per matrix");
     constexpr int RPL = (BMAX + 31) / 32;
-    if (warp < 2) {
-      Tc* M = warp ? Bm : A;
-      bool bad = false;
-      for (int k = 0; k < bb; ++k) {
-        const Tc dkk = M[E * (k * BMAX + k)];
-        if (!(dkk > Tc(0)) || !isfinite(dkk)) {
-          bad = true;
-          break;
-        }
-        const Tc inv = p_rsqrt(dkk);
-        Tc rr[RPL], ri[RPL];  // R_ki of this lane's rows i (scaled)
-#pragma unroll
-        for (int q = 0; q < RPL; ++q) {
-          const int ir = lane + 32 * q;
-          rr[q] = ri[q] = Tc(0);
-          if (ir > k && ir < bb) {
-            rr[q] = M[E * (ir * BMAX + k)] * inv;
-            if constexpr (CPLX) ri[q] = M[E * (ir * BMAX + k) + 1] * inv;
-          }
-        }
-        // columns in groups of CG: all loads of a group before its stores
-        constexpr int CG = CPLX ? 4 : 8;
-        for (int j0 = k + 1; j0 < bb; j0 += CG) {
-          Tc kjr[CG], kji[CG], mr[RPL][CG], mi[RPL][CG];
-#pragma unroll
-          for (int u = 0; u < CG; ++u) {
-            const int jc = j0 + u;
-            kjr[u] = kji[u] = Tc(0);
-            if (jc < bb) {
-              kjr[u] = M[E * (jc * BMAX + k)] * inv;
-              if constexpr (CPLX) kji[u] = M[E * (jc * BMAX + k) + 1] * inv;
-            }
-#pragma unroll
-            for (int q = 0; q < RPL; ++q) {
-              const int ir = lane + 32 * q;
-              mr[q][u] = mi[q][u] = Tc(0);
-              if (ir > k && ir <= jc && jc < bb) {
-                mr[q][u] = M[E * (jc * BMAX + ir)];
-                if constexpr (CPLX) mi[q][u] = M[E * (jc * BMAX + ir) + 1];
-              }
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < CG; ++u) {
-            const int jc = j0 + u;
-#pragma unroll
-            for (int q = 0; q < RPL; ++q) {
-              const int ir = lane + 32 * q;
-              if (ir > k && ir <= jc && jc < bb) {
-                if constexpr (!CPLX) {
-                  M[jc * BMAX + ir] = p_fma(-rr[q], kjr[u], mr[q][u]);
-                } else {
-                  M[2 * (jc * BMAX + ir)] = mr[q][u] - (rr[q] * kjr[u] + ri[q] * kji[u]);
-                  M[2 * (jc * BMAX + ir) + 1] = mi[q][u] - (rr[q] * kji[u] - ri[q] * kjr[u]);
-                }
-              }
-            }
-          }
-        }
-        __syncwarp();  // every lane has read row k
-        if (lane == 0) M[E * (k * BMAX + k)] = dkk * inv;
-#pragma unroll
-        for (int q = 0; q < RPL; ++q) {
-          const int ir = lane + 32 * q;
-          if (ir > k && ir < bb) {
-            M[E * (ir * BMAX + k)] = rr[q];
-            if constexpr (CPLX) M[E * (ir * BMAX + k) + 1] = ri[q];
-          }
-        }
-        __syncwarp();
+    const int mat = warp >> 3, wl = warp & 7;
+    Tc* M = mat ? Bm : A;
+    bool bad = false;
+    for (int k = 0; k < bb; ++k) {
+      const Tc dkk = M[E * (k * BMAX + k)];
+      if (!(dkk > Tc(0)) || !isfinite(dkk)) {
+        bad = true;  // the same for the eight warps of the matrix
+        break;
       }
-      if (bad && lane == 0) s_bad = 1;
+      const Tc inv = p_rsqrt(dkk);
+      Tc rr[RPL], ri[RPL];  // R_ki of this lane's rows i (scaled)
+#pragma unroll
+      for (int q = 0; q < RPL; ++q) {
+        const int ir = lane + 32 * q;
+        rr[q] = ri[q] = Tc(0);
+        if (ir > k && ir < bb) {
+          rr[q] = M[E * (ir * BMAX + k)] * inv;
+          if constexpr (CPLX) ri[q] = M[E * (ir * BMAX + k) + 1] * inv;
+        }
+      }
+      // this warp's columns beyond k: jc = j0 + 8 u, loads before stores
+      const int j0 = k + 1 + ((wl - (k + 1)) & 7);
+      constexpr int CG = (BMAX + 7) / 8;
+      Tc kjr[CG], kji[CG], mr[RPL][CG], mi[RPL][CG];
+#pragma unroll
+      for (int u = 0; u < CG; ++u) {
+        const int jc = j0 + 8 * u;
+        kjr[u] = kji[u] = Tc(0);
+        if (jc < bb) {
+          kjr[u] = M[E * (jc * BMAX + k)] * inv;
+          if constexpr (CPLX) kji[u] = M[E * (jc * BMAX + k) + 1] * inv;
+        }
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+          const int ir = lane + 32 * q;
+          mr[q][u] = mi[q][u] = Tc(0);
+          if (ir > k && ir <= jc && jc < bb) {
+            mr[q][u] = M[E * (jc * BMAX + ir)];
+            if constexpr (CPLX) mi[q][u] = M[E * (jc * BMAX + ir) + 1];
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < CG; ++u) {
+        const int jc = j0 + 8 * u;
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+          const int ir = lane + 32 * q;
+          if (ir > k && ir <= jc && jc < bb) {
+            if constexpr (!CPLX) {
+              M[jc * BMAX + ir] = p_fma(-rr[q], kjr[u], mr[q][u]);
+            } else {
+              M[2 * (jc * BMAX + ir)] = mr[q][u] - (rr[q] * kjr[u] + ri[q] * kji[u]);
+              M[2 * (jc * BMAX + ir) + 1] = mi[q][u] - (rr[q] * kji[u] - ri[q] * kjr[u]);
+            }
+          }
+        }
+      }
+      if (mat)  // warp-uniform: each matrix's eight warps on their own barrier
+        asm volatile("bar.sync 3, 256;\n" ::: "memory");
+      else
+        asm volatile("bar.sync 2, 256;\n" ::: "memory");
+      if (wl == 0 && lane == 0) M[E * (k * BMAX + k)] = dkk * inv;
+      if (lane == 0) {
+#pragma unroll
+        for (int u = 0; u < CG; ++u) {
+          const int jc = j0 + 8 * u;
+          if (jc < bb) {
+            M[E * (jc * BMAX + k)] = kjr[u];
+            if constexpr (CPLX) M[E * (jc * BMAX + k) + 1] = kji[u];
+          }
+        }
+      }
     }
+    if (bad && wl == 0 && lane == 0) s_bad = 1;
     __syncthreads();
   } else
   for (int k = 0; k < bb; ++k) {
