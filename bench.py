@@ -236,7 +236,7 @@ TRAFFIC = {
     "gram_f32": {"kernel": "k_gram32", "source": "k_blocked.cu", "bytes_per_visit": 33.58e6 / 64,
                  "source_sha256": "57e668b5be7f57d6eb8bfbbe721f290317d8ca6ed6d9958b7dd74bdb2bdd7339"},
     "inner_f32": {"kernel": "k_inner", "source": "k_blocked.cu", "bytes_per_visit": 2.668e6 / 64,
-                  "source_sha256": "2627674d84f817159bc5544db90ef684f94d8353ae94e7580bd1a119a5ece1bb"},
+                  "source_sha256": "7d7c84d273e049749c4c1d888e656d1b8c5ea4afe8c0863c0cee36e8f6e9590c"},
     "apply_f32": {"kernel": "k_apply32", "source": "k_blocked.cu", "bytes_per_visit": (50.61e6 + 0.04e6) / 64,
                   "source_sha256": "cb02e515db0e5c8e01f6a67a79bcfb0a30b20d850750175c357073c6f327a158"},
 }
