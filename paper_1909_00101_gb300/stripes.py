@@ -1,10 +1,9 @@
 """A CPU simulation of the multi-GPU stripe algorithm of Sec. 4: the schedule,
 the exchange map and a host driver over processes.
 
-This is not the library's data plane.  Every call of this build gets one GPU,
-so the stripes, their exchange and the application of each pair's
-transformation to the pair's columns (a host matrix product) run on the host
-here, as CPU tensors between processes; the device work of a pair solve can
+This is not the library's data plane: the stripes, their exchange and the
+application of each pair's transformation to the pair's columns (a host
+matrix product) run on the host, as CPU tensors between processes; the device work of a pair solve can
 be the library's (library_pair_solver) or, in the tests, the oracle's.
 
 The columns of F, G and Z are cut into ns = 2 s stripes of equal width (s
