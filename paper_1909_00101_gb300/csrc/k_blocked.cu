@@ -2,15 +2,20 @@
 // Hari-Zimmermann GSVD (Sec. 2.3-2.5 of arXiv 1909.00101), re-designed for
 // sm_103a as three kernels per step instead of the paper's one fused kernel:
 //
-//   k_gram   grid (pair, row split): partial pivot Grams A-hat = [F_p F_q]^* [F_p F_q]
-//            and B-hat = [G_p G_q]^* [G_p G_q] over a slab of rows (FP64: DMMA
-//            m8n8k4 on the tensor pipe; FP32: FFMA with register tiles).
-//   k_inner  grid (pair): fixed-order sum of the partials, Cholesky of A-hat and
-//            B-hat (FP64), then the pointwise implicit HZ on (F-hat, G-hat) in
-//            shared memory with FP64 2x2 parameters one pair per lane, and the
-//            Theta-tilde rescaling that gives Z-tilde = Z-hat Theta-tilde.
-//   k_apply  grid (pair, row tile): [Y_p Y_q] <- [Y_p Y_q] Z-tilde in place for
-//            Y = F, G, Z (FP64: DMMA; FP32: FFMA).
+//   Gram     grid (pair, row split): partial pivot Grams A-hat = [F_p F_q]^* [F_p F_q]
+//            and B-hat = [G_p G_q]^* [G_p G_q] over a slab of rows.  FP32 sweeps:
+//            k_gram32 (upper 8x8 blocks per thread, tiles staged by cp.async);
+//            FP64 sweeps: the exact BF16-digit form in k_ozaki.cu, or k_gram
+//            (DMMA m8n8k4).
+//   pivot    grid (pair): fixed-order sum of the partials, Choleskys of A-hat
+//            and B-hat, the pointwise implicit HZ on (F-hat, G-hat) in shared
+//            memory, and the Theta-tilde rescaling that gives Z-tilde = Z-hat
+//            Theta-tilde.  FP64 sweeps: k_inner2, a two-CTA cluster per pair,
+//            FP64 2x2 parameters one pair per lane; FP32 sweeps: k_inner with
+//            FP32 Choleskys and one pair per half-warp.
+//   apply    grid (pair, row tile): [Y_p Y_q] <- [Y_p Y_q] Z-tilde in place for
+//            Y = F, G, Z.  FP32 sweeps: k_apply32 (4 x 8 outputs per thread);
+//            FP64 sweeps: k_ozaki.cu, or k_apply (DMMA).
 //
 // Splitting the row dimension of the Gram and the apply over many CTAs fills
 // the 152 SMs even when a step has few block pairs (the paper's one CTA per
